@@ -1,0 +1,161 @@
+"""Seeded synthetic workloads (source surfaces and fields).
+
+This module only generates inputs: height maps d1 and complex source fields
+u1 on the uniform source grid, with the shapes, sizes and value distributions
+of the five standard workloads.  It holds none of the diffraction arithmetic
+and is shared, read-only, by the CUDA path's tests, the benchmark and the
+oracle's tests.
+
+Coordinates follow the library's convention x1 = ((n - N/2) p), so the grid is
+centred on the optical axis.  All arrays are row-major [y][x].  u1 is returned
+as complex64 (the precision the CUDA path consumes) so that every consumer sees
+bit-identical field values; d1 is float64 metres.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+NM = 1e-9
+UM = 1e-6
+MM = 1e-3
+
+
+def geometry(n1x, n1y, p1x, p1y, m2x, m2y, p2x, p2y, lam, z0):
+    """Plain dict of the grid geometry used by every consumer (SI units)."""
+    return dict(n1x=int(n1x), n1y=int(n1y), p1x=float(p1x), p1y=float(p1y),
+                m2x=int(m2x), m2y=int(m2y), p2x=float(p2x), p2y=float(p2y),
+                lam=float(lam), z0=float(z0))
+
+
+def coords(n: int, p: float) -> np.ndarray:
+    """Centred sample coordinates (n - N/2) p."""
+    return (np.arange(n) - n // 2) * p
+
+
+# --- surfaces --------------------------------------------------------------
+
+def surface_sinusoid(g, amp, period):
+    """d1 = amp sin(2 pi x / period) sin(2 pi y / period)."""
+    x = coords(g["n1x"], g["p1x"])
+    y = coords(g["n1y"], g["p1y"])
+    return amp * np.sin(2 * np.pi * y / period)[:, None] * np.sin(2 * np.pi * x / period)[None, :]
+
+
+def surface_spherical_cap(g, radius):
+    """Spherical cap sqrt(R^2 - rho^2) - sqrt(R^2 - rho_max^2), rho_max = half-diagonal."""
+    x = coords(g["n1x"], g["p1x"])
+    y = coords(g["n1y"], g["p1y"])
+    rho2 = y[:, None] ** 2 + x[None, :] ** 2
+    rho_max2 = (g["n1x"] / 2 * g["p1x"]) ** 2 + (g["n1y"] / 2 * g["p1y"]) ** 2
+    return np.sqrt(radius ** 2 - rho2) - np.sqrt(radius ** 2 - rho_max2)
+
+
+def surface_smooth_random(g, rng, sigma_samples, pv):
+    """Gaussian noise smoothed by a periodic Gaussian filter of std sigma_samples,
+    rescaled affinely to [0, pv]."""
+    noise = rng.standard_normal((g["n1y"], g["n1x"]))
+    fy = np.fft.fftfreq(g["n1y"])[:, None]
+    fx = np.fft.fftfreq(g["n1x"])[None, :]
+    transfer = np.exp(-2 * np.pi ** 2 * sigma_samples ** 2 * (fx ** 2 + fy ** 2))
+    s = np.fft.ifft2(np.fft.fft2(noise) * transfer).real
+    s -= s.min()
+    return s * (pv / s.max())
+
+
+def surface_tilt_bump(g, tilt_deg, bump_height, bump_sigma):
+    """Plane tilted about the y axis through the centre plus a centred Gaussian bump."""
+    x = coords(g["n1x"], g["p1x"])
+    y = coords(g["n1y"], g["p1y"])
+    tilt = np.broadcast_to(x[None, :] * math.tan(math.radians(tilt_deg)), (g["n1y"], g["n1x"]))
+    rho2 = y[:, None] ** 2 + x[None, :] ** 2
+    return tilt + bump_height * np.exp(-rho2 / (2 * bump_sigma ** 2))
+
+
+# --- fields ------------------------------------------------------------------
+
+def field_unit(g):
+    return np.ones((g["n1y"], g["n1x"]), np.complex64)
+
+
+def field_binary_mask(g, rng, p=0.5):
+    return (rng.random((g["n1y"], g["n1x"])) < p).astype(np.complex64)
+
+
+def field_random_amp_phase(g, rng):
+    amp = rng.random((g["n1y"], g["n1x"]))
+    ph = rng.random((g["n1y"], g["n1x"])) * 2 * np.pi
+    return (amp * np.exp(1j * ph)).astype(np.complex64)
+
+
+def field_unit_random_phase(g, rng):
+    ph = rng.random((g["n1y"], g["n1x"])) * 2 * np.pi
+    return np.exp(1j * ph).astype(np.complex64)
+
+
+# --- the standard workloads ---------------------------------------------------
+
+WORKLOADS = ("sinusoid64", "spherical_cap1024", "smooth_random2048", "rgb_batch24", "tilt_bump4096")
+
+
+def make(name: str, seed: int | None = None, scale: int = 1):
+    """Return (geometry, u1 complex64 [n1y, n1x], d1 float64 [n1y, n1x]).
+
+    name is one of WORKLOADS except the batch (see make_batch).  scale > 1
+    divides the grid sizes by scale while keeping pitch, wavelength and
+    distance (a smaller case of the same workload, for quick parity runs).
+    """
+    if name == "sinusoid64":
+        n = 64 // scale
+        g = geometry(n, n, 10 * UM, 10 * UM, n, n, 10 * UM, 10 * UM, 633 * NM, 0.05)
+        return g, field_unit(g), surface_sinusoid(g, 20 * UM, 320 * UM)
+    if name == "spherical_cap1024":
+        rng = np.random.default_rng(2 if seed is None else seed)
+        n = 1024 // scale
+        g = geometry(n, n, 8 * UM, 8 * UM, n, n, 8 * UM, 8 * UM, 532 * NM, 0.2)
+        return g, field_binary_mask(g, rng), surface_spherical_cap(g, 20 * MM)
+    if name == "smooth_random2048":
+        rng = np.random.default_rng(3 if seed is None else seed)
+        n = 2048 // scale
+        g = geometry(n, n, 4 * UM, 4 * UM, n, n, 4 * UM, 4 * UM, 633 * NM, 0.1)
+        d1 = surface_smooth_random(g, rng, 40.0 / scale, 50 * UM)
+        return g, field_random_amp_phase(g, rng), d1
+    if name == "tilt_bump4096":
+        rng = np.random.default_rng(5 if seed is None else seed)
+        n = 4096 // scale
+        p = 3.74 * UM
+        g = geometry(n, n, p, p, n, n, p, p, 532 * NM, 0.15)
+        return g, field_unit_random_phase(g, rng), surface_tilt_bump(g, 2.0, 30 * UM, 2 * MM)
+    raise ValueError(f"unknown workload {name!r}")
+
+
+def make_batch(seed: int = 4, count: int = 24, sizes=(256, 512, 1024, 2048), pitch=3 * UM):
+    """The RGB batch: count surfaces of sizes drawn from `sizes`, wavelengths
+    cycled over 450/532/633 nm, z0 ~ U[0.05, 0.3] m, sinusoidal or smooth
+    random d1 with amplitude ~ U[5, 50] um, field with uniform amplitude and
+    phase.  Returns a list of (geometry, u1, d1)."""
+    rng = np.random.default_rng(seed)
+    lams = (450 * NM, 532 * NM, 633 * NM)
+    out = []
+    for i in range(count):
+        n = int(rng.choice(sizes))
+        lam = lams[i % 3]
+        z0 = float(rng.uniform(0.05, 0.3))
+        amp = float(rng.uniform(5 * UM, 50 * UM))
+        g = geometry(n, n, pitch, pitch, n, n, pitch, pitch, lam, z0)
+        if rng.random() < 0.5:
+            d1 = surface_sinusoid(g, amp, 320 * UM)
+        else:
+            d1 = surface_smooth_random(g, rng, 40.0, amp)
+        out.append((g, field_random_amp_phase(g, rng), d1))
+    return out
+
+
+def sample_points(g, count: int, seed: int):
+    """`count` distinct destination grid indices drawn without replacement.
+    Returns (mx, my) int32 arrays."""
+    rng = np.random.default_rng(seed)
+    total = g["m2x"] * g["m2y"]
+    flat = rng.choice(total, size=min(count, total), replace=False)
+    return (flat % g["m2x"]).astype(np.int32), (flat // g["m2x"]).astype(np.int32)

@@ -1,0 +1,162 @@
+"""Pins for the FP64 oracle: references that do not reuse the oracle's formula.
+
+Each pin takes an ``eq7(g, u1, d1, points=None)`` callable (the oracle, or a
+deliberately broken copy of it in the mutation test) and returns the relative
+L2 error against a reference computed by another route:
+
+* ``pin_fft_natural_pitch`` -- d1 = 0 at the natural destination pitch
+  p2 = lambda z0 / (N p1): the sum is a centred 2D DFT, computed with numpy's
+  FFT (Sec. 2, Eq. 7 with d1 = 0 reduces to single-FFT Fresnel diffraction).
+* ``pin_planar_shift`` -- d1 = c: Eq. 7 equals single-FFT planar Fresnel
+  propagation over z0 - c (numpy FFT at that distance's natural pitch), times
+  exp(ik c) times the two factors the approximations of Eqs. 5-6 leave:
+  (z0 - c)/z0 and exp(ik|x2|^2 (1/z0 - 1/(z0 - c))/2).
+* ``pin_gaussian`` -- a Gaussian source on d1 = c: the continuous integral
+  has a closed form; the discrete sum matches it to truncation and aliasing
+  error (chosen below 1e-9).
+* ``pin_terraces`` -- piecewise-constant d1: by linearity the result is a
+  sum over terraces of separable transforms, each computed as two dense 1D
+  DFT matrix products per axis (exercises a per-sample r0 and the x/y roles
+  with non-square grids and unequal pitches).
+* ``pin_single_sample_modulus`` -- one nonzero sample: |u2| = p1x p1y |u1| /
+  (lambda z0) at every destination point.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def _coords(n, p):
+    return (np.arange(n) - n // 2) * p
+
+
+def rel_l2(a, b):
+    a = np.asarray(a)
+    b = np.asarray(b)
+    return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
+
+
+def centred_dft2(f):
+    """F[m'] = sum_n f[n] exp(-2 pi i n' m'/N) with centred indices (library FFT)."""
+    return np.fft.fftshift(np.fft.fft2(np.fft.ifftshift(f)))
+
+
+def planar_fresnel_fft(u1, p1x, p1y, lam, z):
+    """Textbook single-FFT Fresnel propagation over distance z (Goodman, Ch. 4):
+    U(x2) = e^{ikz} e^{ik|x2|^2/2z} / (i lam z) * FT[u1 e^{ik|x1|^2/2z}] at
+    the natural pitch p2 = lam z / (N p1).  Returns (U, p2x, p2y)."""
+    n1y, n1x = u1.shape
+    k = 2 * np.pi / lam
+    x = _coords(n1x, p1x)[None, :]
+    y = _coords(n1y, p1y)[:, None]
+    p2x = lam * z / (n1x * p1x)
+    p2y = lam * z / (n1y * p1y)
+    X = _coords(n1x, p2x)[None, :]
+    Y = _coords(n1y, p2y)[:, None]
+    F = centred_dft2(u1 * np.exp(1j * k * (x ** 2 + y ** 2) / (2 * z))) * p1x * p1y
+    U = np.exp(1j * k * z) * np.exp(1j * k * (X ** 2 + Y ** 2) / (2 * z)) / (1j * lam * z) * F
+    return U, p2x, p2y
+
+
+def _rng_field(rng, shape):
+    return (rng.standard_normal(shape) + 1j * rng.standard_normal(shape)).astype(np.complex64)
+
+
+def pin_fft_natural_pitch(eq7, n1x=24, n1y=16, p1x=10e-6, p1y=7e-6, lam=633e-9, z0=0.05, seed=11):
+    rng = np.random.default_rng(seed)
+    u1 = _rng_field(rng, (n1y, n1x)).astype(np.complex128)
+    U, p2x, p2y = planar_fresnel_fft(u1, p1x, p1y, lam, z0)
+    g = dict(n1x=n1x, n1y=n1y, p1x=p1x, p1y=p1y, m2x=n1x, m2y=n1y, p2x=p2x, p2y=p2y,
+             lam=lam, z0=z0)
+    return rel_l2(eq7(g, u1, np.zeros((n1y, n1x))), U)
+
+
+def pin_planar_shift(eq7, c=0.3e-3, n1x=20, n1y=16, p1x=10e-6, p1y=8e-6, lam=633e-9, z0=0.05,
+                     seed=12):
+    rng = np.random.default_rng(seed)
+    u1 = _rng_field(rng, (n1y, n1x)).astype(np.complex128)
+    z = z0 - c
+    U, p2x, p2y = planar_fresnel_fft(u1, p1x, p1y, lam, z)
+    k = 2 * np.pi / lam
+    X = _coords(n1x, p2x)[None, :]
+    Y = _coords(n1y, p2y)[:, None]
+    ref = U * np.exp(1j * k * c) * (z / z0) * np.exp(
+        1j * k * (X ** 2 + Y ** 2) * (1 / z0 - 1 / z) / 2)
+    g = dict(n1x=n1x, n1y=n1y, p1x=p1x, p1y=p1y, m2x=n1x, m2y=n1y, p2x=p2x, p2y=p2y,
+             lam=lam, z0=z0)
+    return rel_l2(eq7(g, u1, np.full((n1y, n1x), c)), ref)
+
+
+def pin_gaussian(eq7, c=0.2e-3, n1=64, p1=10e-6, m2x=40, m2y=36, p2x=11e-6, p2y=13e-6,
+                 lam=633e-9, z0=0.05):
+    """Gaussian u1 = exp(-|x1|^2/w0^2) on the plane d1 = c (w0 = aperture/10).
+    With r0 = z0 - c and a = 1/w0^2 - ik/(2 r0), the integral over x1 of
+    u1 e^{ik|x1|^2/2r0} e^{-ik x1.x2/r0} is (pi/a) exp(-(k/r0)^2 |x2|^2/(4a))."""
+    k = 2 * np.pi / lam
+    w0 = n1 * p1 / 10
+    x = _coords(n1, p1)
+    u1 = np.exp(-(x[None, :] ** 2 + x[:, None] ** 2) / w0 ** 2).astype(np.complex128)
+    r0 = z0 - c
+    a = 1 / w0 ** 2 - 1j * k / (2 * r0)
+    X = _coords(m2x, p2x)[None, :]
+    Y = _coords(m2y, p2y)[:, None]
+    r2 = X ** 2 + Y ** 2
+    integral = (np.pi / a) * np.exp(-(k / r0) ** 2 * r2 / (4 * a))
+    ref = np.exp(1j * k * (z0 + r2 / (2 * z0))) / (1j * lam * z0) * integral
+    g = dict(n1x=n1, n1y=n1, p1x=p1, p1y=p1, m2x=m2x, m2y=m2y, p2x=p2x, p2y=p2y, lam=lam, z0=z0)
+    return rel_l2(eq7(g, u1, np.full((n1, n1), c)), ref)
+
+
+def pin_terraces(eq7, n1x=18, n1y=14, p1x=9e-6, p1y=6e-6, m2x=12, m2y=22, p2x=15e-6, p2y=5e-6,
+                 lam=532e-9, z0=0.04, seed=13):
+    """d1 takes four constant values on random masks.  For one terrace with
+    height c and r0 = z0 - c the sum factorises per axis:
+      S_c = Ey (M_c o u1 o Cy Cx^T) Ex^T,  Ex[m, n] = exp(-ik x1[n] x2[m] / r0),
+    with the source chirp split as Cy[ny] Cx[nx] = exp(ik(x^2 + y^2)/(2 r0))."""
+    rng = np.random.default_rng(seed)
+    k = 2 * np.pi / lam
+    u1 = _rng_field(rng, (n1y, n1x)).astype(np.complex128)
+    heights = np.array([-0.4e-3, 0.0, 0.25e-3, 0.9e-3])
+    label = rng.integers(0, heights.size, (n1y, n1x))
+    d1 = heights[label]
+    x1 = _coords(n1x, p1x)
+    y1 = _coords(n1y, p1y)
+    x2 = _coords(m2x, p2x)
+    y2 = _coords(m2y, p2y)
+    total = np.zeros((m2y, m2x), np.complex128)
+    for t, c in enumerate(heights):
+        r0 = z0 - c
+        Ex = np.exp(-1j * k * np.outer(x2, x1) / r0)          # [m2x, n1x]
+        Ey = np.exp(-1j * k * np.outer(y2, y1) / r0)          # [m2y, n1y]
+        chirp = np.outer(np.exp(1j * k * y1 ** 2 / (2 * r0)), np.exp(1j * k * x1 ** 2 / (2 * r0)))
+        f = np.where(label == t, u1 * chirp, 0)
+        total += Ey @ f @ Ex.T
+    X, Y = x2[None, :], y2[:, None]
+    outer = np.exp(1j * k * (z0 + (X ** 2 + Y ** 2) / (2 * z0))) / (1j * lam * z0)
+    ref = outer * p1x * p1y * total
+    g = dict(n1x=n1x, n1y=n1y, p1x=p1x, p1y=p1y, m2x=m2x, m2y=m2y, p2x=p2x, p2y=p2y,
+             lam=lam, z0=z0)
+    return rel_l2(eq7(g, u1, d1), ref)
+
+
+def pin_single_sample_modulus(eq7, n1=16, p1=10e-6, lam=633e-9, z0=0.05, seed=14):
+    rng = np.random.default_rng(seed)
+    u1 = np.zeros((n1, n1), np.complex128)
+    a = 0.7 - 0.3j
+    u1[3, 11] = a
+    d1 = rng.uniform(-50e-6, 50e-6, (n1, n1))
+    g = dict(n1x=n1, n1y=n1, p1x=p1, p1y=p1, m2x=n1, m2y=n1, p2x=12e-6, p2y=9e-6, lam=lam, z0=z0)
+    out = eq7(g, u1, d1)
+    expect = p1 * p1 * abs(a) / (lam * z0)
+    return float(np.max(np.abs(np.abs(out) - expect)) / expect)
+
+
+# Tolerances: the phases k z0 ~ 5e5 rad carry FP64 rounding of ~1e-10 rad, so
+# agreement is bounded near 1e-10; every planted mistake gives O(1) errors.
+ALL_PINS = {
+    "fft_natural_pitch": (pin_fft_natural_pitch, 1e-9),
+    "planar_shift": (pin_planar_shift, 1e-9),
+    "gaussian": (pin_gaussian, 1e-9),
+    "terraces": (pin_terraces, 1e-9),
+    "single_sample_modulus": (pin_single_sample_modulus, 1e-12),
+}
