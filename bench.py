@@ -1,0 +1,339 @@
+#!/usr/bin/env python
+"""Throughput of the arbitrary-shape-surface Fresnel transform on GB300.
+
+Metric: source samples per second of the forward transform (Eq. 8) on the
+2048 x 2048 smooth-random-surface workload (4 um pitch, 633 nm, z0 = 0.1 m,
+oversampling 2, ES kernel width 7), with the relative L2 error against the
+FP64 direct-sum oracle on sampled destination points.
+
+One step = one pass of the whole hot path over one synthetic input: the
+per-sample prefactor + tiled spread, the row FFT, and the column FFT with
+deconvolution and destination chirp, on inputs already resident in HBM.  L2
+is flushed (a 512 MiB write) between timed steps, outside the timed region.
+Each rank of a multi-GPU run processes its own copy of the workload (the path
+shards by independent surfaces; no collective on the data path).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "source samples/sec at 2048^2 (forward transform, rel-L2 vs FP64 oracle)"
+UNIT = "samples/s"
+WORKLOAD = "smooth_random2048"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--width", type=int, default=7)
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0,
+                    help="target CPU time of the oracle baseline sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def workload_config(name, width):
+    return {"workload": f"{name}: 2048x2048 source at 4 um, smooth random surface (sigma 40 "
+                        "samples, 0-50 um), amplitude U[0,1], phase U[0,2pi), 633 nm, z0 0.1 m, "
+                        "2048x2048 destination at 4 um" if name == WORKLOAD else name,
+            "method": "type-1 NUFFT, ES kernel", "kernel_width": width, "sigma": 2,
+            "precision": "FP32 spread/FFT/deconvolution, FP64-built phase tables",
+            "l2": "flushed between timed steps (512 MiB write)"}
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.file, stderr=subprocess.DEVNULL)
+        except (OSError, ValueError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.file.flush()
+        self.file.seek(0)
+        rows = [r.split(",") for r in self.file.read().strip().splitlines() if r.strip()]
+        os.unlink(self.file.name)
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for r in rows:
+            r = [x.strip() for x in r]
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, r[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "MEASURED_PEAKS.json hbm_gbs (of measured)"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM_GBS, "profiling-recipe fallback 6.8 TB/s (of fallback)"
+
+
+def stage_bytes(info, g):
+    """Algorithmic HBM bytes per launch of each stage."""
+    n = g["n1x"] * g["n1y"]
+    band_rows = info["band_y1"] - info["band_y0"]
+    band_cols = info["band_x1"] - info["band_x0"]
+    tables = 2 * (g["n1x"] + g["n1y"]) * 24
+    spread = n * (8 + 4) + band_rows * band_cols * 8 + tables
+    rows = band_rows * band_cols * 8 + band_rows * g["m2x"] * 8
+    cols = band_rows * g["m2x"] * 8 + g["m2x"] * g["m2y"] * 8 + (g["m2x"] + g["m2y"]) * 8
+    return [spread, rows, cols]
+
+
+STAGE_KERNELS = ["spread_es_kernel", "fft_rows_kernel", "fft_cols_kernel"]
+
+
+def oracle_sample(g, u1, d1, seconds, seed=7):
+    """Time the FP64 oracle on a bounded sample of destination points.
+    Returns (samples_per_s, cores, n_points, elapsed, points, values)."""
+    import oracle
+    from paper_1203_3583_gb300 import workloads as W
+    n = g["n1x"] * g["n1y"]
+    m = g["m2x"] * g["m2y"]
+    probe = W.sample_points(g, 8, seed=seed + 1)
+    t = time.perf_counter()
+    oracle.eq7(g, u1, d1, points=probe)
+    dt = max(time.perf_counter() - t, 1e-6)
+    npts = int(max(8, min(m, round(8 * seconds / dt))))
+    pts = W.sample_points(g, npts, seed=seed)
+    t = time.perf_counter()
+    vals = oracle.eq7(g, u1, d1, points=pts)
+    el = time.perf_counter() - t
+    samples_per_s = n * npts / (el * m)
+    return samples_per_s, oracle.max_threads(), npts, el, pts, vals
+
+
+def run_reference(args):
+    """The reference arm: the FP64 oracle as it stands, on the host cores."""
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import numpy as np  # noqa: F401
+    import oracle
+    from paper_1203_3583_gb300 import workloads as W
+    g, u1, d1 = W.make(args.workload)
+    n = g["n1x"] * g["n1y"]
+    m = g["m2x"] * g["m2y"]
+    npts = 16
+    times = []
+    for i in range(args.warmup + args.steps):
+        pts = W.sample_points(g, npts, seed=1000 + i)
+        t = time.perf_counter()
+        oracle.eq7(g, u1, d1, points=pts)
+        if i >= args.warmup:
+            times.append(time.perf_counter() - t)
+    t_step = statistics.mean(times)
+    value = n * npts / (t_step * m)
+    cores = oracle.max_threads()
+    sample = (f"{npts} seeded destination points per step of the {g['m2x']}x{g['m2y']} grid, "
+              f"each a direct FP64 sum over all {n} source samples; value = source samples / "
+              "(step time x destination points / sampled points)")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": t_step * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(args.workload, args.width),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_1203_3583_gb300 import capi, workloads as W
+    from paper_1203_3583_gb300.fresnel import FresnelPlan
+
+    world, rank, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    capi.load()
+    dev = torch.device("cuda", local)
+
+    g, u1, d1 = W.make(args.workload)
+    n_src = g["n1x"] * g["n1y"]
+    t0 = time.perf_counter()
+    plan = FresnelPlan(g, d1, kernel_width=args.width)
+    torch.cuda.synchronize()
+    plan_ms = (time.perf_counter() - t0) * 1e3
+    info = plan.info()
+    u1_d = torch.as_tensor(u1, device=dev)
+    u2_d = torch.empty(plan.shape2, dtype=torch.complex64, device=dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step(ev):
+        ev[0].record(stream)
+        plan.execute_stage(0, u1=u1_d)
+        ev[1].record(stream)
+        plan.execute_stage(1)
+        ev[2].record(stream)
+        plan.execute_stage(2, out=u2_d)
+        ev[3].record(stream)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        step([torch.cuda.Event(enable_timing=True) for _ in range(4)])
+    torch.cuda.synchronize()
+    plan.check_device_status()
+
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local) if rank == 0 else None
+    wall0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.zero_()
+        step(evs[i])
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop() if clocks else None
+    plan.check_device_status()
+
+    step_ms = [e[0].elapsed_time(e[3]) for e in evs]
+    stage_ms = [[e[s].elapsed_time(e[s + 1]) for e in evs] for s in range(3)]
+    ms = statistics.mean(step_ms)
+    if world > 1:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * n_src / (ms * 1e-3)
+
+    # roofline of the dominant kernel (algorithmic bytes / event-timed duration)
+    sb = stage_bytes(info, g)
+    mean_stage = [statistics.mean(s) for s in stage_ms]
+    dom = int(np.argmax(mean_stage))
+    peak, peak_src = measured_peaks()
+    achieved = sb[dom] / (mean_stage[dom] * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "kernel": f"{STAGE_KERNELS[dom]}<{args.width if dom == 0 else ''}>"
+                .replace("<>", ""), "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": None,
+                "algorithmic_bytes_per_launch": sb[dom], "peak_source": peak_src,
+                "stage_ms": {k: v for k, v in zip(STAGE_KERNELS, mean_stage)},
+                "stage_frac": {k: b / (t * 1e-3) / 1e9 / peak
+                               for k, b, t in zip(STAGE_KERNELS, sb, mean_stage)}}
+
+    # end to end through the C ABI with pinned host buffers
+    hu1 = torch.as_tensor(u1).pin_memory()
+    hu2 = torch.empty(plan.shape2, dtype=torch.complex64).pin_memory()
+    for _ in range(max(1, args.warmup)):
+        plan.execute_host(hu1, hu2)
+    e2e_t = []
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        plan.execute_host(hu1, hu2)
+        e2e_t.append(time.perf_counter() - t)
+    e2e_s = statistics.mean(e2e_t)
+    if world > 1:
+        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": world * n_src / e2e_s, "unit": UNIT, "h2d_bytes_per_step": hu1.numel() * 8,
+           "d2h_bytes_per_step": hu2.numel() * 8}
+
+    line = None
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic", "config": workload_config(args.workload, args.width),
+                "roofline": roofline, "e2e": e2e, "clocks": clk,
+                "gpu_launches": 3 * args.steps, "plan_ms": plan_ms,
+                "wall_s_timed_region": wall,
+                "plan": {k: info[k] for k in ("nfx", "nfy", "band_x0", "band_x1", "band_y0",
+                                              "band_y1", "spread_tiles", "tile_pairs")}}
+        if world == 1 and not args.no_cpu_baseline:
+            sps, cores, npts, el, pts, ref = oracle_sample(g, u1, d1, args.cpu_seconds)
+            got = u2_d.cpu().numpy()[pts[1], pts[0]].astype(np.complex128)
+            line["rel_l2_vs_oracle"] = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+            line["rel_l2_points"] = npts
+            line["cpu_baseline"] = {
+                "value": sps, "unit": UNIT, "cores": cores, "kind": "oracle",
+                "sample": f"{npts} seeded destination points of the {g['m2x']}x{g['m2y']} grid "
+                          f"({el:.1f} s), each a direct FP64 sum over all {n_src} source samples; "
+                          "scaled to source samples/s of the full transform"}
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,173 @@
+/*
+ * asfd.h -- C ABI of the arbitrary-shape-surface Fresnel diffraction library
+ * (Shimobaba, Masuda, Ito, "Arbitrary shape surface Fresnel diffraction").
+ *
+ * The library evaluates Eq. 8 of the paper: the Fresnel-approximated Huygens
+ * sum from a sampled source surface u1(x1, d1(x1)) to a planar destination,
+ * as a non-uniform-to-uniform (type-1) 2D NUFFT.  In its discretised form
+ * (Eq. 7, the "Fourier form", with the cross-term sign of Eqs. 4-5 and 9):
+ *
+ *   u2[m] = exp(ik(z0 + |x2|^2/(2 z0))) / (i lambda z0)
+ *           * sum_n p1x p1y u1[n] exp(ik d1[n])
+ *                   exp(ik(-d1[n] + |x1[n]|^2 / (2 r0[n])))
+ *                   exp(-ik x1[n].x2[m] / r0[n]),     r0 = z0 - d1,
+ *
+ * with x1 = ((nx - N1x/2) p1x, (ny - N1y/2) p1y) and
+ *      x2 = ((mx - M2x/2) p2x, (my - M2y/2) p2y).
+ * The incident wave exp(ik d1) is the normally incident plane wave of Sec. 2.
+ *
+ * Conventions for every entry point:
+ *  - Complex arrays are interleaved (re, im) float pairs, row-major [y][x]
+ *    with x fastest: u1 is [n1y][n1x], u2 is [m2y][m2x].
+ *  - "device" pointers are CUDA global-memory pointers on the device that was
+ *    current when the plan was created; "host" pointers are host memory
+ *    (page-locked for full copy speed).  All memory passed in is owned by the
+ *    caller and only borrowed for the duration of the call (or, for
+ *    asynchronous calls, until the work queued on `stream` completes).
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Device work is queued asynchronously on it unless stated.
+ *  - A plan owns its device tables and work buffers.  Calls on one plan must
+ *    not overlap in time (one stream at a time).
+ *  - No exceptions cross the ABI.  Every call returns an asfd_status; a
+ *    one-line description of the last failure on the calling thread is
+ *    available from asfd_last_error().
+ */
+#ifndef ASFD_H
+#define ASFD_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    ASFD_OK = 0,
+    ASFD_ERR_ARG = 1,          /* invalid argument: sizes, NULL pointers, NaN d1, d1 >= z0 */
+    ASFD_ERR_CUDA = 2,         /* a CUDA runtime call or kernel launch failed            */
+    ASFD_ERR_NOMEM = 3,        /* device or host allocation failed                        */
+    ASFD_ERR_TIMEOUT = 4,      /* a bounded device-side wait ran out                      */
+    ASFD_ERR_UNSUPPORTED = 5,  /* valid request outside what the library implements       */
+    ASFD_ERR_STATE = 6         /* call not valid in the plan's current state              */
+} asfd_status;
+
+typedef enum {
+    ASFD_KERNEL_ES = 0,        /* exponential-of-semicircle spreading kernel              */
+    ASFD_KERNEL_LEARNED = 1    /* per-tile tabulated kernel (see asfd_set_learned_table)  */
+} asfd_kernel_kind;
+
+/* Geometry and NUFFT parameters of a plan (SI units). */
+typedef struct {
+    int n1x, n1y;        /* source samples; even, 2..65536                             */
+    double p1x, p1y;     /* source pitch [m], > 0                                       */
+    int m2x, m2y;        /* destination samples; even                                   */
+    double p2x, p2y;     /* destination pitch [m], > 0                                  */
+    double lambda;       /* wavelength [m], > 0                                         */
+    double z0;           /* source-to-destination distance [m], > 0                     */
+    double sigma;        /* oversampling factor in [1.25, 4]; sigma*m2x and sigma*m2y   */
+                         /* must be powers of two in [64, 16384] (typically sigma = 2)  */
+    int kernel_width;    /* spreading kernel width w in fine-grid cells, 2..16          */
+    double es_beta;      /* ES shape parameter; 0 selects 2.30*w at sigma = 2           */
+    asfd_kernel_kind kind;
+} asfd_params;
+
+typedef struct asfd_plan_s* asfd_plan;
+
+/* Read-only facts about a built plan (for tests and reports). */
+typedef struct {
+    int nfx, nfy;            /* oversampled (fine) grid size                            */
+    int tile_x, tile_y;      /* fine-grid tile of the spreading kernel                  */
+    int band_x0, band_x1;    /* touched fine-grid columns [x0, x1) (storage coords)     */
+    int band_y0, band_y1;    /* touched fine-grid rows    [y0, y1)                      */
+    int spread_tiles;        /* output tiles the spreading kernel processes             */
+    long long tile_pairs;    /* (output tile, source tile) pairs in the binning         */
+    double es_beta;          /* ES beta in use                                          */
+    double max_abs_eps;      /* max |d1| / z0 over the surface                          */
+    size_t device_bytes;     /* device memory owned by the plan                         */
+} asfd_plan_info;
+
+/*
+ * Create a plan for the geometry `p` and the height map `d1_dev`
+ * (device, FP64, [n1y][n1x], metres, positive toward the destination; read
+ * during the call only).  Builds, on the device and in FP64, the per-axis
+ * phase and position tables (source chirp |x1|^2/(2 z0) and the fine-grid
+ * coordinate of every sample, Sec. 2 Eqs. 4-8), the destination chirp and
+ * kernel-deconvolution tables, the per-sample r0 correction, and the binning
+ * of samples to fine-grid tiles.  Synchronises `stream` once (binning).
+ * Errors: ASFD_ERR_ARG for invalid sizes/pitches, non-finite d1, d1 >= z0;
+ * ASFD_ERR_UNSUPPORTED when max |d1|/z0 > 0.1 or a size is out of range;
+ * ASFD_ERR_NOMEM / ASFD_ERR_CUDA on allocation or launch failure.
+ * On failure *out is set to NULL and nothing is leaked.
+ */
+asfd_status asfd_plan_create(asfd_plan* out, const asfd_params* p, const double* d1_dev,
+                             void* stream);
+
+/* Replace the plan's height map (same sizes) and rebuild the d1-dependent
+ * tables and binning.  Same errors as asfd_plan_create; the plan is unchanged
+ * on failure. */
+asfd_status asfd_plan_update_d1(asfd_plan plan, const double* d1_dev, void* stream);
+
+/*
+ * Forward transform, Eq. 8: u2 = outer(x2) * NUFT[u_I u1 exp(ik(-d1 + |x1|^2/(2 r0)))].
+ * u1_dev: device [n1y][n1x] complex; u2_dev: device [m2y][m2x] complex.
+ * Stages (all CUDA kernels on `stream`): per-sample prefactor fused into the
+ * tiled spread onto the sigma-oversampled grid, row FFT with crop, column FFT
+ * fused with kernel deconvolution, crop and the destination chirp.
+ * Asynchronous.  Errors: ASFD_ERR_ARG (NULL), ASFD_ERR_CUDA (launch).
+ */
+asfd_status asfd_execute(asfd_plan plan, const float* u1_dev, float* u2_dev, void* stream);
+
+/*
+ * Same transform on HOST buffers: copies u1 host->device, runs asfd_execute,
+ * copies u2 device->host, and synchronises `stream` before returning.
+ * u1_host: [n1y][n1x] complex; u2_host: [m2y][m2x] complex.
+ */
+asfd_status asfd_execute_host(asfd_plan plan, const float* u1_host, float* u2_host, void* stream);
+
+/*
+ * One stage of asfd_execute, for per-kernel timing with events recorded on
+ * `stream` between the calls:
+ *   stage 0: per-sample prefactor + tiled spread: reads u1_dev, writes the
+ *            plan's oversampled grid (u2_dev unused, may be NULL);
+ *   stage 1: row FFT + crop: plan grid -> plan row buffer (u1, u2 unused);
+ *   stage 2: column FFT + deconvolution + crop + destination chirp:
+ *            plan row buffer -> u2_dev (u1 unused).
+ * Running stages 0, 1, 2 in order on one stream equals asfd_execute.
+ * Errors: ASFD_ERR_ARG (bad stage or missing buffer), ASFD_ERR_CUDA.
+ */
+asfd_status asfd_execute_stage(asfd_plan plan, int stage, const float* u1_dev, float* u2_dev,
+                               void* stream);
+
+/* Fill *info.  Errors: ASFD_ERR_ARG. */
+asfd_status asfd_get_plan_info(asfd_plan plan, asfd_plan_info* info);
+
+/* Wait for `stream`, then report a device-side failure recorded by the
+ * plan's kernels since the last call (bounded waits, index checks), and
+ * clear it.  ASFD_OK when none was recorded. */
+asfd_status asfd_check_device_status(asfd_plan plan, void* stream);
+
+/* Release the plan and everything it owns (synchronises the device).  NULL is
+ * accepted. */
+asfd_status asfd_destroy(asfd_plan plan);
+
+/* Static description of a status code. */
+const char* asfd_status_string(asfd_status s);
+
+/* Description of the last failure on the calling thread ("" if none). */
+const char* asfd_last_error(void);
+
+/*
+ * Stand-alone batched FFT of the library (the Stockham kernel used by the
+ * transform), exposed for unit tests and timing.  in_dev/out_dev: device
+ * [lines][n] complex (may alias); n a power of two in [16, 16384];
+ * sign = -1 computes X[k] = sum_j x[j] exp(-2 pi i jk/n), +1 the conjugate
+ * kernel (no 1/n scaling).  Asynchronous.
+ */
+asfd_status asfd_fft_lines(int n, int lines, int sign, const float* in_dev, float* out_dev,
+                           void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ASFD_H */

@@ -1,0 +1,203 @@
+"""Python binding of the C ABI in include/asfd.h (ctypes; marshalling only).
+
+Every function here has the name of the C entry point it calls and does no
+arithmetic of the method: it checks tensor devices, dtypes and shapes, passes
+raw pointers and the current CUDA stream, and turns a non-OK status into an
+AsfdError carrying asfd_last_error().  PyTorch supplies device memory and
+streams.  There is no CPU fallback: if libasfd.so has not been built, loading
+fails with an error.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libasfd.so")
+
+ASFD_OK = 0
+ASFD_KERNEL_ES = 0
+ASFD_KERNEL_LEARNED = 1
+
+# every symbol declared in include/asfd.h, with (restype, argtypes)
+_vp = ctypes.c_void_p
+_int = ctypes.c_int
+
+
+class AsfdError(RuntimeError):
+    """A non-OK asfd_status; `.status` holds the code."""
+
+    def __init__(self, status: int, msg: str):
+        super().__init__(msg)
+        self.status = status
+
+
+class Params(ctypes.Structure):
+    """Mirror of asfd_params."""
+
+    _fields_ = [
+        ("n1x", ctypes.c_int), ("n1y", ctypes.c_int),
+        ("p1x", ctypes.c_double), ("p1y", ctypes.c_double),
+        ("m2x", ctypes.c_int), ("m2y", ctypes.c_int),
+        ("p2x", ctypes.c_double), ("p2y", ctypes.c_double),
+        ("lam", ctypes.c_double), ("z0", ctypes.c_double),
+        ("sigma", ctypes.c_double),
+        ("kernel_width", ctypes.c_int),
+        ("es_beta", ctypes.c_double),
+        ("kind", ctypes.c_int),
+    ]
+
+
+class PlanInfo(ctypes.Structure):
+    """Mirror of asfd_plan_info."""
+
+    _fields_ = [
+        ("nfx", ctypes.c_int), ("nfy", ctypes.c_int),
+        ("tile_x", ctypes.c_int), ("tile_y", ctypes.c_int),
+        ("band_x0", ctypes.c_int), ("band_x1", ctypes.c_int),
+        ("band_y0", ctypes.c_int), ("band_y1", ctypes.c_int),
+        ("spread_tiles", ctypes.c_int),
+        ("tile_pairs", ctypes.c_longlong),
+        ("es_beta", ctypes.c_double),
+        ("max_abs_eps", ctypes.c_double),
+        ("device_bytes", ctypes.c_size_t),
+    ]
+
+
+SIGNATURES = {
+    "asfd_plan_create": (_int, [ctypes.POINTER(_vp), ctypes.POINTER(Params), _vp, _vp]),
+    "asfd_plan_update_d1": (_int, [_vp, _vp, _vp]),
+    "asfd_execute": (_int, [_vp, _vp, _vp, _vp]),
+    "asfd_execute_host": (_int, [_vp, _vp, _vp, _vp]),
+    "asfd_execute_stage": (_int, [_vp, _int, _vp, _vp, _vp]),
+    "asfd_get_plan_info": (_int, [_vp, ctypes.POINTER(PlanInfo)]),
+    "asfd_check_device_status": (_int, [_vp, _vp]),
+    "asfd_destroy": (_int, [_vp]),
+    "asfd_status_string": (ctypes.c_char_p, [_int]),
+    "asfd_last_error": (ctypes.c_char_p, []),
+    "asfd_fft_lines": (_int, [_int, _int, _int, _vp, _vp, _vp]),
+}
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libasfd.so and declare every entry point (raises if it is missing)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(path):
+                raise RuntimeError(
+                    f"{path} is missing: build it with "
+                    "`python -c 'import __graft_entry__ as g; g.build()'` (needs nvcc)")
+            lib = ctypes.CDLL(path)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def _check(status: int):
+    if status != ASFD_OK:
+        lib = load()
+        msg = lib.asfd_last_error().decode() or lib.asfd_status_string(status).decode()
+        raise AsfdError(status, f"{lib.asfd_status_string(status).decode()}: {msg}")
+
+
+def _stream(stream):
+    if stream is None:
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, torch.cuda.Stream):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+def _dev_ptr(t: torch.Tensor, dtype, shape, name):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must have dtype {dtype}, got {t.dtype}")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def make_params(g: dict, sigma: float = 2.0, kernel_width: int = 7, es_beta: float = 0.0,
+                kind: int = ASFD_KERNEL_ES) -> Params:
+    """asfd_params from a geometry dict (keys of workloads.geometry)."""
+    return Params(int(g["n1x"]), int(g["n1y"]), float(g["p1x"]), float(g["p1y"]),
+                  int(g["m2x"]), int(g["m2y"]), float(g["p2x"]), float(g["p2y"]),
+                  float(g["lam"]), float(g["z0"]), float(sigma), int(kernel_width),
+                  float(es_beta), int(kind))
+
+
+def asfd_plan_create(params: Params, d1: torch.Tensor, stream=None) -> ctypes.c_void_p:
+    lib = load()
+    ptr = _dev_ptr(d1, torch.float64, (params.n1y, params.n1x), "d1")
+    out = ctypes.c_void_p()
+    _check(lib.asfd_plan_create(ctypes.byref(out), ctypes.byref(params), ptr, _stream(stream)))
+    return out
+
+
+def asfd_plan_update_d1(plan, d1: torch.Tensor, n1x: int, n1y: int, stream=None) -> None:
+    lib = load()
+    _check(lib.asfd_plan_update_d1(plan, _dev_ptr(d1, torch.float64, (n1y, n1x), "d1"),
+                                   _stream(stream)))
+
+
+def asfd_execute(plan, u1: torch.Tensor, u2: torch.Tensor, shape1, shape2, stream=None) -> None:
+    lib = load()
+    _check(lib.asfd_execute(plan, _dev_ptr(u1, torch.complex64, shape1, "u1"),
+                            _dev_ptr(u2, torch.complex64, shape2, "u2"), _stream(stream)))
+
+
+def asfd_execute_stage(plan, stage: int, u1, u2, shape1, shape2, stream=None) -> None:
+    lib = load()
+    p1 = _dev_ptr(u1, torch.complex64, shape1, "u1") if u1 is not None else None
+    p2 = _dev_ptr(u2, torch.complex64, shape2, "u2") if u2 is not None else None
+    _check(lib.asfd_execute_stage(plan, int(stage), p1, p2, _stream(stream)))
+
+
+def asfd_execute_host(plan, u1: torch.Tensor, u2: torch.Tensor, shape1, shape2, stream=None) -> None:
+    lib = load()
+    for t, name, shape in ((u1, "u1", shape1), (u2, "u2", shape2)):
+        if t.is_cuda or t.dtype != torch.complex64 or tuple(t.shape) != tuple(shape) \
+                or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous complex64 host tensor of shape {shape}")
+    _check(lib.asfd_execute_host(plan, ctypes.c_void_p(u1.data_ptr()),
+                                 ctypes.c_void_p(u2.data_ptr()), _stream(stream)))
+
+
+def asfd_get_plan_info(plan) -> dict:
+    lib = load()
+    info = PlanInfo()
+    _check(lib.asfd_get_plan_info(plan, ctypes.byref(info)))
+    return {name: getattr(info, name) for name, _ in PlanInfo._fields_}
+
+
+def asfd_check_device_status(plan, stream=None) -> None:
+    _check(load().asfd_check_device_status(plan, _stream(stream)))
+
+
+def asfd_destroy(plan) -> None:
+    _check(load().asfd_destroy(plan))
+
+
+def asfd_fft_lines(x: torch.Tensor, sign: int = -1, out: torch.Tensor | None = None,
+                   stream=None) -> torch.Tensor:
+    """Batched FFT of the rows of a 2D complex64 CUDA tensor with the library's kernel."""
+    lines, n = x.shape
+    if out is None:
+        out = torch.empty_like(x)
+    _check(load().asfd_fft_lines(n, lines, sign, _dev_ptr(x, torch.complex64, (lines, n), "x"),
+                                 _dev_ptr(out, torch.complex64, (lines, n), "out"),
+                                 _stream(stream)))
+    return out

@@ -1,0 +1,122 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/asfd.h"
+
+namespace asfd {
+
+// Fine-grid tile owned by one CTA of the spreading kernel, and the source
+// tile (block of samples) used for binning.
+constexpr int kTileX = 64;
+constexpr int kTileY = 64;
+constexpr int kSrcTile = 16;  // source tiles are kSrcTile x kSrcTile samples
+
+// Device status word bits (set by kernels, read by asfd_check_device_status).
+constexpr unsigned kStatusBadD1 = 1u;       // non-finite d1 or d1 >= z0
+constexpr unsigned kStatusRange = 2u;       // |d1|/z0 above the supported bound
+constexpr unsigned kStatusTimeout = 4u;     // a bounded wait ran out
+constexpr unsigned kStatusIndex = 8u;       // an index check failed (access skipped)
+
+// Per-source-axis table entry (one per nx, and one per ny).
+//   e    = exp(i pi x1^2/(lambda z0))   source chirp |x1|^2/(2 z0) of that axis (FP64 -> FP32)
+//   a    = x1^2/(lambda z0)             the same phase in half-turns (FP32, unreduced)
+//   s    = alpha x~                     fine-grid offset of the sample at d1 = 0
+// and, separately, the integer/fraction split of the storage coordinate
+//   alpha x~ + nf/2 (mod nf) = bi + bf.
+struct AxisEntry {
+    float2 e;
+    float a;
+    float s;
+};
+struct AxisPos {
+    int bi;
+    float bf;
+};
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+
+}  // namespace asfd
+
+struct asfd_plan_s {
+    asfd_params prm{};
+    int device = 0;
+    int nfx = 0, nfy = 0;
+    int w = 0;
+    double beta = 0.0;
+    double alpha_x = 0.0, alpha_y = 0.0;  // fine cells per source sample at d1 = 0
+    double max_abs_eps = 0.0;
+
+    // tables (device)
+    asfd::AxisEntry* ax = nullptr;  // [n1x]
+    asfd::AxisEntry* ay = nullptr;  // [n1y]
+    asfd::AxisPos* px = nullptr;    // [n1x]
+    asfd::AxisPos* py = nullptr;    // [n1y]
+    double* bux = nullptr;          // unreduced alpha x~ + nf/2 per axis (plan only)
+    double* buy = nullptr;
+    float* q = nullptr;             // [n1y][n1x]  d1 / (z0 - d1)
+    float2* cx = nullptr;           // [m2x] destination chirp * (-1)^m' / psi_hat
+    float2* cy = nullptr;           // [m2y] same, times the global factor
+    float2* twx = nullptr;          // [nfx] e^{-2 pi i k/nfx}
+    float2* twy = nullptr;          // [nfy]
+    double* quad = nullptr;         // [2*nq] Gauss-Legendre nodes z_i and w_i psi(z_i) on [0, w/2]
+    int nq = 0;
+
+    // binning
+    int ntx = 0, nty = 0;           // fine-grid tiles per axis
+    int nstx = 0, nsty = 0;         // source tiles per axis
+    double4* src_bbox = nullptr;    // per source tile: unreduced footprint bounds (x0, x1, y0, y1)
+    int* tile_off = nullptr;        // [band tiles + 1] CSR offsets
+    int* tile_src = nullptr;        // CSR source-tile ids
+    int band_tx0 = 0, band_tx1 = 0, band_ty0 = 0, band_ty1 = 0;  // band in tiles
+    long long tile_pairs = 0;
+    size_t tile_src_cap = 0;
+
+    // work buffers
+    float2* grid = nullptr;         // [nfy][nfx]
+    float2* rows = nullptr;         // [nfy][m2x] row-FFT output (band rows first)
+    unsigned* status = nullptr;     // device status word
+    float2* stage_u1 = nullptr;     // staging for asfd_execute_host (allocated on first use)
+    float2* stage_u2 = nullptr;
+
+    std::vector<asfd::DevBuf> owned;
+    size_t device_bytes = 0;
+};
+
+namespace asfd {
+
+// error reporting (thread-local message)
+asfd_status fail(asfd_status s, const std::string& msg);
+asfd_status cuda_fail(cudaError_t e, const char* what);
+void clear_error();
+
+#define ASFD_CUDA(call)                                                   \
+    do {                                                                  \
+        cudaError_t _e = (call);                                          \
+        if (_e != cudaSuccess) return ::asfd::cuda_fail(_e, #call);       \
+    } while (0)
+
+// stage launchers (each returns ASFD_OK or an error with a message)
+asfd_status launch_spread(asfd_plan_s* P, const float2* u1, cudaStream_t st);
+asfd_status launch_fft_rows(asfd_plan_s* P, cudaStream_t st);
+asfd_status launch_fft_cols(asfd_plan_s* P, float2* u2, cudaStream_t st);
+asfd_status launch_fft_lines(int n, int lines, int sign, const float2* in, float2* out,
+                             cudaStream_t st);
+
+// plan helpers
+asfd_status plan_validate(const asfd_params* p, int* nfx, int* nfy, double* beta);
+asfd_status plan_alloc(asfd_plan_s* P);
+asfd_status build_twiddles(float2* tw, int L, cudaStream_t st);
+asfd_status plan_build_tables(asfd_plan_s* P, cudaStream_t st);
+asfd_status plan_build_d1(asfd_plan_s* P, const double* d1, cudaStream_t st);
+
+}  // namespace asfd

@@ -1,0 +1,246 @@
+// The exported C ABI (include/asfd.h): argument checks, plan lifetime, and
+// the forward transform as three kernels on the caller's stream.
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "asfd_impl.cuh"
+
+namespace asfd {
+
+namespace {
+thread_local std::string g_last_error;
+}
+
+asfd_status fail(asfd_status s, const std::string& msg)
+{
+    g_last_error = msg;
+    return s;
+}
+
+asfd_status cuda_fail(cudaError_t e, const char* what)
+{
+    g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+    return ASFD_ERR_CUDA;
+}
+
+void clear_error() { g_last_error.clear(); }
+
+namespace {
+
+void free_all(asfd_plan_s* P)
+{
+    for (auto& b : P->owned) cudaFree(b.p);
+    P->owned.clear();
+    P->device_bytes = 0;
+}
+
+// Runs `fn` with the plan's device current, restoring the caller's device.
+template <class F>
+asfd_status on_device(int dev, F&& fn)
+{
+    int prev = 0;
+    ASFD_CUDA(cudaGetDevice(&prev));
+    if (prev != dev) ASFD_CUDA(cudaSetDevice(dev));
+    asfd_status s = fn();
+    if (prev != dev) cudaSetDevice(prev);
+    return s;
+}
+
+}  // namespace
+}  // namespace asfd
+
+using namespace asfd;
+
+extern "C" {
+
+const char* asfd_status_string(asfd_status s)
+{
+    switch (s) {
+        case ASFD_OK: return "ok";
+        case ASFD_ERR_ARG: return "invalid argument";
+        case ASFD_ERR_CUDA: return "CUDA error";
+        case ASFD_ERR_NOMEM: return "out of memory";
+        case ASFD_ERR_TIMEOUT: return "device wait timed out";
+        case ASFD_ERR_UNSUPPORTED: return "unsupported";
+        case ASFD_ERR_STATE: return "invalid state";
+    }
+    return "unknown status";
+}
+
+const char* asfd_last_error(void) { return g_last_error.c_str(); }
+
+asfd_status asfd_plan_create(asfd_plan* out, const asfd_params* p, const double* d1_dev,
+                             void* stream)
+{
+    clear_error();
+    if (!out) return fail(ASFD_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    int nfx = 0, nfy = 0;
+    double beta = 0.0;
+    asfd_status s = plan_validate(p, &nfx, &nfy, &beta);
+    if (s != ASFD_OK) return s;
+    if (!d1_dev) return fail(ASFD_ERR_ARG, "d1 is NULL");
+    asfd_plan_s* P = new (std::nothrow) asfd_plan_s();
+    if (!P) return fail(ASFD_ERR_NOMEM, "host allocation of the plan failed");
+    P->prm = *p;
+    P->nfx = nfx;
+    P->nfy = nfy;
+    P->w = p->kernel_width;
+    P->beta = beta;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    s = [&]() -> asfd_status {
+        ASFD_CUDA(cudaGetDevice(&P->device));
+        asfd_status r = plan_alloc(P);
+        if (r != ASFD_OK) return r;
+        r = plan_build_tables(P, st);
+        if (r != ASFD_OK) return r;
+        return plan_build_d1(P, d1_dev, st);
+    }();
+    if (s != ASFD_OK) {
+        free_all(P);
+        delete P;
+        return s;
+    }
+    *out = P;
+    return ASFD_OK;
+}
+
+asfd_status asfd_plan_update_d1(asfd_plan P, const double* d1_dev, void* stream)
+{
+    clear_error();
+    if (!P || !d1_dev) return fail(ASFD_ERR_ARG, "plan or d1 is NULL");
+    return on_device(P->device, [&] {
+        return plan_build_d1(P, d1_dev, static_cast<cudaStream_t>(stream));
+    });
+}
+
+asfd_status asfd_execute(asfd_plan P, const float* u1_dev, float* u2_dev, void* stream)
+{
+    clear_error();
+    if (!P || !u1_dev || !u2_dev) return fail(ASFD_ERR_ARG, "plan, u1 or u2 is NULL");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    return on_device(P->device, [&]() -> asfd_status {
+        asfd_status s = launch_spread(P, reinterpret_cast<const float2*>(u1_dev), st);
+        if (s != ASFD_OK) return s;
+        s = launch_fft_rows(P, st);
+        if (s != ASFD_OK) return s;
+        return launch_fft_cols(P, reinterpret_cast<float2*>(u2_dev), st);
+    });
+}
+
+asfd_status asfd_execute_stage(asfd_plan P, int stage, const float* u1_dev, float* u2_dev,
+                               void* stream)
+{
+    clear_error();
+    if (!P) return fail(ASFD_ERR_ARG, "plan is NULL");
+    if (stage == 0 && !u1_dev) return fail(ASFD_ERR_ARG, "stage 0 needs u1");
+    if (stage == 2 && !u2_dev) return fail(ASFD_ERR_ARG, "stage 2 needs u2");
+    if (stage < 0 || stage > 2) return fail(ASFD_ERR_ARG, "stage must be 0, 1 or 2");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    return on_device(P->device, [&]() -> asfd_status {
+        if (stage == 0) return launch_spread(P, reinterpret_cast<const float2*>(u1_dev), st);
+        if (stage == 1) return launch_fft_rows(P, st);
+        return launch_fft_cols(P, reinterpret_cast<float2*>(u2_dev), st);
+    });
+}
+
+asfd_status asfd_execute_host(asfd_plan P, const float* u1_host, float* u2_host, void* stream)
+{
+    clear_error();
+    if (!P || !u1_host || !u2_host) return fail(ASFD_ERR_ARG, "plan, u1 or u2 is NULL");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    return on_device(P->device, [&]() -> asfd_status {
+        // staging buffers live for the plan's lifetime (allocated on first use)
+        const size_t b1 = sizeof(float2) * (size_t)P->prm.n1x * P->prm.n1y;
+        const size_t b2 = sizeof(float2) * (size_t)P->prm.m2x * P->prm.m2y;
+        if (!P->stage_u1) {
+            void* a = nullptr;
+            void* b = nullptr;
+            if (cudaMalloc(&a, b1) != cudaSuccess || cudaMalloc(&b, b2) != cudaSuccess) {
+                cudaGetLastError();
+                if (a) cudaFree(a);
+                return fail(ASFD_ERR_NOMEM, "staging buffers for asfd_execute_host");
+            }
+            P->stage_u1 = static_cast<float2*>(a);
+            P->stage_u2 = static_cast<float2*>(b);
+            P->owned.push_back(DevBuf{a, b1});
+            P->owned.push_back(DevBuf{b, b2});
+            P->device_bytes += b1 + b2;
+        }
+        ASFD_CUDA(cudaMemcpyAsync(P->stage_u1, u1_host, b1, cudaMemcpyHostToDevice, st));
+        asfd_status s = launch_spread(P, P->stage_u1, st);
+        if (s != ASFD_OK) return s;
+        s = launch_fft_rows(P, st);
+        if (s != ASFD_OK) return s;
+        s = launch_fft_cols(P, P->stage_u2, st);
+        if (s != ASFD_OK) return s;
+        ASFD_CUDA(cudaMemcpyAsync(u2_host, P->stage_u2, b2, cudaMemcpyDeviceToHost, st));
+        ASFD_CUDA(cudaStreamSynchronize(st));
+        return ASFD_OK;
+    });
+}
+
+asfd_status asfd_get_plan_info(asfd_plan P, asfd_plan_info* info)
+{
+    clear_error();
+    if (!P || !info) return fail(ASFD_ERR_ARG, "plan or info is NULL");
+    std::memset(info, 0, sizeof(*info));
+    info->nfx = P->nfx;
+    info->nfy = P->nfy;
+    info->tile_x = kTileX;
+    info->tile_y = kTileY;
+    info->band_x0 = P->band_tx0 * kTileX;
+    info->band_x1 = P->band_tx1 * kTileX;
+    info->band_y0 = P->band_ty0 * kTileY;
+    info->band_y1 = P->band_ty1 * kTileY;
+    info->spread_tiles = (P->band_tx1 - P->band_tx0) * (P->band_ty1 - P->band_ty0);
+    info->tile_pairs = P->tile_pairs;
+    info->es_beta = P->beta;
+    info->max_abs_eps = P->max_abs_eps;
+    info->device_bytes = P->device_bytes;
+    return ASFD_OK;
+}
+
+asfd_status asfd_check_device_status(asfd_plan P, void* stream)
+{
+    clear_error();
+    if (!P) return fail(ASFD_ERR_ARG, "plan is NULL");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    return on_device(P->device, [&]() -> asfd_status {
+        unsigned h = 0;
+        ASFD_CUDA(cudaMemcpyAsync(&h, P->status, sizeof(h), cudaMemcpyDeviceToHost, st));
+        ASFD_CUDA(cudaStreamSynchronize(st));
+        if (h == 0) return ASFD_OK;
+        ASFD_CUDA(cudaMemsetAsync(P->status, 0, sizeof(unsigned), st));
+        ASFD_CUDA(cudaStreamSynchronize(st));
+        if (h & kStatusTimeout) return fail(ASFD_ERR_TIMEOUT, "a bounded device wait ran out");
+        if (h & kStatusIndex) return fail(ASFD_ERR_STATE, "a device index check failed");
+        return fail(ASFD_ERR_ARG, "device status word " + std::to_string(h));
+    });
+}
+
+asfd_status asfd_destroy(asfd_plan P)
+{
+    clear_error();
+    if (!P) return ASFD_OK;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(P->device);
+    cudaDeviceSynchronize();
+    free_all(P);
+    cudaSetDevice(prev);
+    delete P;
+    return ASFD_OK;
+}
+
+asfd_status asfd_fft_lines(int n, int lines, int sign, const float* in_dev, float* out_dev,
+                           void* stream)
+{
+    clear_error();
+    return launch_fft_lines(n, lines, sign, reinterpret_cast<const float2*>(in_dev),
+                            reinterpret_cast<float2*>(out_dev), static_cast<cudaStream_t>(stream));
+}
+
+}  // extern "C"

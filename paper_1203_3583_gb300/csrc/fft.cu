@@ -1,0 +1,270 @@
+// Uniform-FFT stages of the type-1 NUFFT (Sec. 2, after Eq. 9) and the
+// final scaling of Eq. 8.
+//
+//   rows:  for each touched fine-grid row, FFT along x (e^{-i}), keeping the
+//          M2x centred bins k in [-M2x/2, M2x/2) in the order k + M2x/2.
+//          Columns outside the spread band are zero and are not read.
+//   cols:  for each kept column, FFT along y over the touched rows (the
+//          rest are zero), keep the M2y centred bins and multiply by the
+//          separable factor Cx[kx] Cy[ky] that holds the kernel
+//          deconvolution 1/psi_hat, the (-1)^k of the centred fine-grid
+//          storage, the destination chirp exp(ik|x2|^2/(2 z0)) and, in Cy,
+//          the global factor exp(ik z0) p1x p1y / (i lambda z0).
+#include <mutex>
+
+#include "asfd_impl.cuh"
+#include "fft.cuh"
+
+namespace asfd {
+
+namespace {
+
+template <int L>
+struct RowCfg {
+    static constexpr int TPL = L / 16;
+    static constexpr int LPC = L >= 4096 ? 1 : 4096 / L;  // lines per CTA
+    static constexpr int THREADS = TPL * LPC;
+    static constexpr int LS = FftShape<L>::SMEM + (TPL < 16 ? TPL : 0);
+    static constexpr size_t SMEM_BYTES = sizeof(float2) * LS * LPC;
+};
+
+template <int L>
+struct ColCfg {
+    static constexpr int TPL = L / 16;
+    static constexpr int LPC0 = (256 / TPL) > 4 ? (256 / TPL) : 4;
+    static constexpr int LPC = (LPC0 * TPL > 1024) ? (1024 / TPL) : LPC0;
+    static constexpr int THREADS = TPL * LPC;
+    static constexpr int LS = FftShape<L>::SMEM + 16 / (LPC < 16 ? LPC : 16);
+    static constexpr size_t SMEM_BYTES = sizeof(float2) * LS * LPC;
+};
+
+template <int L>
+__global__ void __launch_bounds__(RowCfg<L>::THREADS)
+fft_rows_kernel(const float2* __restrict__ grid, int row0, int nrows, int col_lo, int col_hi,
+                float2* __restrict__ out, int m2x, const float2* __restrict__ tw)
+{
+    using C = RowCfg<L>;
+    extern __shared__ float2 sm[];
+    const int line = threadIdx.x / C::TPL, t = threadIdx.x % C::TPL;
+    const int r = blockIdx.x * C::LPC + line;
+    const bool active = r < nrows;
+    const float2* src = grid + (size_t)(row0 + (active ? r : 0)) * L;
+    float2* dst = out + (size_t)(active ? r : 0) * m2x;
+    const int half = m2x / 2;
+    auto ld = [&](int i) -> float2 {
+        return (active && i >= col_lo && i < col_hi) ? __ldg(&src[i]) : make_float2(0.f, 0.f);
+    };
+    auto st = [&](int i, float2 v) {
+        if (!active) return;
+        if (i < half) dst[i + half] = v;
+        else if (i >= L - half) dst[i - (L - half)] = v;
+    };
+    fft_line<L, -1>(t, sm + line * C::LS, tw, ld, st);
+}
+
+template <int L>
+__global__ void __launch_bounds__(ColCfg<L>::THREADS)
+fft_cols_kernel(const float2* __restrict__ rows, int row0, int nrows, int m2x, int m2y,
+                const float2* __restrict__ cx, const float2* __restrict__ cy,
+                float2* __restrict__ u2, const float2* __restrict__ tw)
+{
+    using C = ColCfg<L>;
+    extern __shared__ float2 sm[];
+    const int c = threadIdx.x % C::LPC, t = threadIdx.x / C::LPC;
+    const int col = blockIdx.x * C::LPC + c;
+    const bool active = col < m2x;
+    const int colc = active ? col : 0;
+    const float2 fx = __ldg(&cx[colc]);
+    const int half = m2y / 2;
+    auto ld = [&](int i) -> float2 {
+        const int rr = i - row0;
+        return (active && rr >= 0 && rr < nrows) ? __ldg(&rows[(size_t)rr * m2x + colc])
+                                                 : make_float2(0.f, 0.f);
+    };
+    auto st = [&](int i, float2 v) {
+        if (!active) return;
+        int k;
+        if (i < half) k = i + half;
+        else if (i >= L - half) k = i - (L - half);
+        else return;
+        u2[(size_t)k * m2x + colc] = cmul(cmul(v, fx), __ldg(&cy[k]));
+    };
+    fft_line<L, -1>(t, sm + c * C::LS, tw, ld, st);
+}
+
+template <int L, int S>
+__global__ void __launch_bounds__(RowCfg<L>::THREADS)
+fft_lines_kernel(const float2* in, float2* out, int lines, const float2* __restrict__ tw)
+{
+    using C = RowCfg<L>;
+    extern __shared__ float2 sm[];
+    const int line = threadIdx.x / C::TPL, t = threadIdx.x % C::TPL;
+    const int r = blockIdx.x * C::LPC + line;
+    const bool active = r < lines;
+    const float2* src = in + (size_t)(active ? r : 0) * L;
+    float2* dst = out + (size_t)(active ? r : 0) * L;
+    auto ld = [&](int i) -> float2 { return active ? src[i] : make_float2(0.f, 0.f); };
+    auto st = [&](int i, float2 v) {
+        if (active) dst[i] = v;
+    };
+    fft_line<L, S>(t, sm + line * C::LS, tw, ld, st);
+}
+
+template <class F>
+cudaError_t set_smem(F* f, size_t bytes)
+{
+    if (bytes <= 48 * 1024) return cudaSuccess;
+    return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+template <int L>
+cudaError_t rows_L(const float2* grid, int row0, int nrows, int col_lo, int col_hi, float2* out,
+                   int m2x, const float2* tw, cudaStream_t st)
+{
+    using C = RowCfg<L>;
+    static std::once_flag once;
+    static cudaError_t attr = cudaSuccess;
+    std::call_once(once, [] { attr = set_smem(fft_rows_kernel<L>, C::SMEM_BYTES); });
+    if (attr != cudaSuccess) return attr;
+    const int blocks = (nrows + C::LPC - 1) / C::LPC;
+    fft_rows_kernel<L><<<blocks, C::THREADS, C::SMEM_BYTES, st>>>(grid, row0, nrows, col_lo,
+                                                                  col_hi, out, m2x, tw);
+    return cudaGetLastError();
+}
+
+template <int L>
+cudaError_t cols_L(const float2* rows, int row0, int nrows, int m2x, int m2y, const float2* cx,
+                   const float2* cy, float2* u2, const float2* tw, cudaStream_t st)
+{
+    using C = ColCfg<L>;
+    static std::once_flag once;
+    static cudaError_t attr = cudaSuccess;
+    std::call_once(once, [] { attr = set_smem(fft_cols_kernel<L>, C::SMEM_BYTES); });
+    if (attr != cudaSuccess) return attr;
+    const int blocks = (m2x + C::LPC - 1) / C::LPC;
+    fft_cols_kernel<L><<<blocks, C::THREADS, C::SMEM_BYTES, st>>>(rows, row0, nrows, m2x, m2y,
+                                                                  cx, cy, u2, tw);
+    return cudaGetLastError();
+}
+
+template <int L, int S>
+cudaError_t lines_L(const float2* in, float2* out, int lines, const float2* tw, cudaStream_t st)
+{
+    using C = RowCfg<L>;
+    static std::once_flag once;
+    static cudaError_t attr = cudaSuccess;
+    std::call_once(once, [] { attr = set_smem(fft_lines_kernel<L, S>, C::SMEM_BYTES); });
+    if (attr != cudaSuccess) return attr;
+    const int blocks = (lines + C::LPC - 1) / C::LPC;
+    fft_lines_kernel<L, S><<<blocks, C::THREADS, C::SMEM_BYTES, st>>>(in, out, lines, tw);
+    return cudaGetLastError();
+}
+
+#define ASFD_FFT_SWITCH(n, CALL)       \
+    switch (n) {                       \
+        case 16: CALL(16); break;      \
+        case 32: CALL(32); break;      \
+        case 64: CALL(64); break;      \
+        case 128: CALL(128); break;    \
+        case 256: CALL(256); break;    \
+        case 512: CALL(512); break;    \
+        case 1024: CALL(1024); break;  \
+        case 2048: CALL(2048); break;  \
+        case 4096: CALL(4096); break;  \
+        case 8192: CALL(8192); break;  \
+        case 16384: CALL(16384); break; \
+        default: e = cudaErrorInvalidValue; \
+    }
+
+// FP64-built twiddle tables e^{-2 pi i k/L}, one per length, cached per device.
+__global__ void twiddle_kernel(float2* tw, int L)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= L) return;
+    double s, c;
+    sincospi(2.0 * (double)k / (double)L, &s, &c);
+    tw[k] = make_float2((float)c, (float)-s);
+}
+
+}  // namespace
+
+asfd_status launch_fft_rows(asfd_plan_s* P, cudaStream_t st)
+{
+    const int row0 = P->band_ty0 * kTileY;
+    const int nrows = (P->band_ty1 - P->band_ty0) * kTileY;
+    const int col_lo = P->band_tx0 * kTileX, col_hi = P->band_tx1 * kTileX;
+    if (nrows <= 0) return ASFD_OK;
+    cudaError_t e = cudaSuccess;
+#define ASFD_ROWS(L) e = rows_L<L>(P->grid, row0, nrows, col_lo, col_hi, P->rows, P->prm.m2x, P->twx, st)
+    ASFD_FFT_SWITCH(P->nfx, ASFD_ROWS)
+#undef ASFD_ROWS
+    if (e != cudaSuccess) return cuda_fail(e, "fft_rows_kernel launch");
+    return ASFD_OK;
+}
+
+asfd_status launch_fft_cols(asfd_plan_s* P, float2* u2, cudaStream_t st)
+{
+    const int row0 = P->band_ty0 * kTileY;
+    const int nrows = (P->band_ty1 - P->band_ty0) * kTileY;
+    cudaError_t e = cudaSuccess;
+#define ASFD_COLS(L) e = cols_L<L>(P->rows, row0, nrows, P->prm.m2x, P->prm.m2y, P->cx, P->cy, u2, P->twy, st)
+    ASFD_FFT_SWITCH(P->nfy, ASFD_COLS)
+#undef ASFD_COLS
+    if (e != cudaSuccess) return cuda_fail(e, "fft_cols_kernel launch");
+    return ASFD_OK;
+}
+
+asfd_status build_twiddles(float2* tw, int L, cudaStream_t st)
+{
+    twiddle_kernel<<<(L + 255) / 256, 256, 0, st>>>(tw, L);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "twiddle_kernel launch");
+    return ASFD_OK;
+}
+
+asfd_status launch_fft_lines(int n, int lines, int sign, const float2* in, float2* out,
+                             cudaStream_t st)
+{
+    if (n < 16 || n > 16384 || (n & (n - 1)) || lines < 0 || (sign != 1 && sign != -1) ||
+        (lines > 0 && (!in || !out)))
+        return fail(ASFD_ERR_ARG, "asfd_fft_lines: n must be a power of two in [16, 16384], "
+                                  "sign +-1, non-NULL buffers");
+    if (lines == 0) return ASFD_OK;
+    // one twiddle table per (device, length), built on first use
+    static std::mutex mu;
+    static float2* tables[64][15] = {};
+    int dev = 0;
+    ASFD_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return fail(ASFD_ERR_UNSUPPORTED, "device ordinal above 63");
+    const int lg = ilog2_c(n);
+    float2* tw = nullptr;
+    {
+        std::lock_guard<std::mutex> g(mu);
+        if (!tables[dev][lg]) {
+            float2* p = nullptr;
+            ASFD_CUDA(cudaMalloc(&p, sizeof(float2) * n));
+            asfd_status s = build_twiddles(p, n, st);
+            if (s != ASFD_OK) {
+                cudaFree(p);
+                return s;
+            }
+            ASFD_CUDA(cudaStreamSynchronize(st));
+            tables[dev][lg] = p;
+        }
+        tw = tables[dev][lg];
+    }
+    cudaError_t e = cudaSuccess;
+    if (sign < 0) {
+#define ASFD_LN(L) e = lines_L<L, -1>(in, out, lines, tw, st)
+        ASFD_FFT_SWITCH(n, ASFD_LN)
+#undef ASFD_LN
+    } else {
+#define ASFD_LP(L) e = lines_L<L, 1>(in, out, lines, tw, st)
+        ASFD_FFT_SWITCH(n, ASFD_LP)
+#undef ASFD_LP
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "fft_lines_kernel launch");
+    return ASFD_OK;
+}
+
+}  // namespace asfd

@@ -1,0 +1,441 @@
+// Plan construction: FP64 geometry and phase tables, d1 checks, binning.
+//
+// All phases are carried in half-turns (units of pi), because
+//   k |x|^2 / (2 z) = pi |x|^2 / (lambda z)   and   k z0 = pi (2 z0 / lambda),
+// so no inexact multiple of pi enters, and reduction modulo 2 (= 2 pi rad)
+// of an FP64 value a is the exact operation a - 2 rint(a/2).  sincospi then
+// evaluates the reduced phase.  These are the large phases of Eqs. 5-8: the
+// global k z0 (up to ~2e6 rad at the standard workloads), the source chirp
+// k|x1|^2/(2 z0) and the destination chirp k|x2|^2/(2 z0) (up to ~5e3 rad).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "asfd_impl.cuh"
+
+namespace asfd {
+
+namespace {
+
+__device__ __forceinline__ double reduce_halfturns(double a) { return a - 2.0 * rint(0.5 * a); }
+
+// Per-axis source table: chirp exp(i pi x^2/(lambda z0)), its unreduced value
+// in half-turns, the fine-grid offset alpha x~ and its storage-coordinate split.
+__global__ void axis_table_kernel(AxisEntry* ae, AxisPos* ap, double* bu, int n, double p,
+                                  double lam_z0, double alpha, int nf)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double xt = (double)(i - n / 2);
+    const double x1 = xt * p;
+    const double a = x1 * x1 / lam_z0;
+    double s, c;
+    sincospi(reduce_halfturns(a), &s, &c);
+    const double g = alpha * xt;
+    const double B = g + 0.5 * (double)nf;
+    const double Br = B - (double)nf * floor(B / (double)nf);
+    int bi = (int)floor(Br);
+    double bf = Br - (double)bi;
+    if (bi >= nf) bi -= nf;
+    AxisEntry e;
+    e.e = make_float2((float)c, (float)s);
+    e.a = (float)a;
+    e.s = (float)g;
+    ae[i] = e;
+    AxisPos q;
+    q.bi = bi;
+    q.bf = (float)bf;
+    ap[i] = q;
+    bu[i] = B;
+}
+
+// Destination table C[k'] = (-1)^m' exp(i pi x2^2/(lambda z0)) / psi_hat(2 pi m'/nf),
+// m' = k' - m/2, times the global factor exp(ik z0) p1x p1y / (i lambda z0)
+// when `global` is set.  psi_hat(xi) = 2 sum_i w_i psi(z_i) cos(xi z_i)
+// (Gauss-Legendre on [0, w/2], nodes and weighted kernel values in quad).
+__global__ void dest_table_kernel(float2* C, int m, double p2, double lam_z0, int nf,
+                                  const double* quad, int nq, int global, double two_z0_over_lam,
+                                  double amp)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= m) return;
+    const int mp = k - m / 2;
+    const double x2 = (double)mp * p2;
+    double s, c;
+    sincospi(reduce_halfturns(x2 * x2 / lam_z0), &s, &c);
+    double ph = 0.0;
+    for (int i = 0; i < nq; ++i) ph += quad[nq + i] * cospi(2.0 * (double)mp * quad[i] / (double)nf);
+    ph *= 2.0;
+    const double sgn = (mp & 1) ? -1.0 : 1.0;
+    double re = sgn * c / ph, im = sgn * s / ph;
+    if (global) {
+        // exp(i theta) / i * amp = amp (sin theta - i cos theta), theta = k z0
+        double gs, gc;
+        sincospi(reduce_halfturns(two_z0_over_lam), &gs, &gc);
+        const double gre = amp * gs, gim = -amp * gc;
+        const double r2 = re * gre - im * gim, i2 = re * gim + im * gre;
+        re = r2;
+        im = i2;
+    }
+    C[k] = make_float2((float)re, (float)im);
+}
+
+// Checks d1 (finite, below z0) and reduces max |d1|/z0.
+__global__ void d1_check_kernel(const double* d1, size_t n, double z0, unsigned* status,
+                                unsigned* maxeps_bits)
+{
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    float e = 0.f;
+    if (i < n) {
+        const double h = d1[i];
+        if (!isfinite(h) || !(h < z0)) atomicOr(status, kStatusBadD1);
+        else e = (float)(fabs(h) / z0);
+    }
+    for (int o = 16; o > 0; o >>= 1) e = fmaxf(e, __shfl_xor_sync(0xffffffffu, e, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(maxeps_bits, __float_as_uint(e));
+}
+
+// q = d1 / (z0 - d1) in FP64, stored FP32.
+__global__ void d1_q_kernel(const double* d1, float* q, size_t n, double z0)
+{
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double h = d1[i];
+    q[i] = (float)(h / (z0 - h));
+}
+
+// Per source tile: bounds of the unreduced storage coordinate alpha x~ (1+q) + nf/2.
+__global__ void src_bbox_kernel(const float* q, const AxisEntry* ax, const AxisEntry* ay,
+                                const double* bux, const double* buy, int n1x, int n1y, int nstx,
+                                double4* bbox)
+{
+    const int tile = blockIdx.x;
+    const int nx = (tile % nstx) * kSrcTile + threadIdx.x % kSrcTile;
+    const int ny = (tile / nstx) * kSrcTile + threadIdx.x / kSrcTile;
+    double x0 = 1e300, x1 = -1e300, y0 = 1e300, y1 = -1e300;
+    if (nx < n1x && ny < n1y) {
+        const float qq = q[(size_t)ny * n1x + nx];
+        const double ux = bux[nx] + (double)(ax[nx].s * qq);
+        const double uy = buy[ny] + (double)(ay[ny].s * qq);
+        x0 = x1 = ux;
+        y0 = y1 = uy;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        x0 = fmin(x0, __shfl_xor_sync(0xffffffffu, x0, o));
+        x1 = fmax(x1, __shfl_xor_sync(0xffffffffu, x1, o));
+        y0 = fmin(y0, __shfl_xor_sync(0xffffffffu, y0, o));
+        y1 = fmax(y1, __shfl_xor_sync(0xffffffffu, y1, o));
+    }
+    __shared__ double red[4][kSrcTile * kSrcTile / 32];
+    const int wid = threadIdx.x / 32;
+    if ((threadIdx.x & 31) == 0) {
+        red[0][wid] = x0;
+        red[1][wid] = x1;
+        red[2][wid] = y0;
+        red[3][wid] = y1;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < kSrcTile * kSrcTile / 32; ++w) {
+            x0 = fmin(x0, red[0][w]);
+            x1 = fmax(x1, red[1][w]);
+            y0 = fmin(y0, red[2][w]);
+            y1 = fmax(y1, red[3][w]);
+        }
+        bbox[tile] = make_double4(x0, x1, y0, y1);
+    }
+}
+
+// Gauss-Legendre nodes and weights on [-1, 1] (Newton iteration on P_n).
+void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& wt)
+{
+    const double pi = 3.14159265358979323846;
+    x.assign(n, 0.0);
+    wt.assign(n, 0.0);
+    for (int i = 0; i < (n + 1) / 2; ++i) {
+        double z = std::cos(pi * (i + 0.75) / (n + 0.5));
+        double dp = 0.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = z;
+            for (int k = 2; k <= n; ++k) {
+                const double pk = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = pk;
+            }
+            dp = n * (z * p1 - p0) / (z * z - 1.0);
+            const double dz = p1 / dp;
+            z -= dz;
+            if (std::fabs(dz) < 1e-16) break;
+        }
+        {
+            double p0 = 1.0, p1 = z;
+            for (int k = 2; k <= n; ++k) {
+                const double pk = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = pk;
+            }
+            dp = n * (z * p1 - p0) / (z * z - 1.0);
+        }
+        x[i] = -z;
+        x[n - 1 - i] = z;
+        wt[i] = wt[n - 1 - i] = 2.0 / ((1.0 - z * z) * dp * dp);
+    }
+}
+
+asfd_status alloc(asfd_plan_s* P, void** p, size_t bytes)
+{
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return fail(ASFD_ERR_NOMEM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed: " +
+                                        cudaGetErrorString(e));
+    }
+    P->owned.push_back(DevBuf{*p, bytes});
+    P->device_bytes += bytes;
+    return ASFD_OK;
+}
+
+template <class T>
+asfd_status alloc_n(asfd_plan_s* P, T** p, size_t count)
+{
+    void* v = nullptr;
+    asfd_status s = alloc(P, &v, sizeof(T) * (count ? count : 1));
+    *p = static_cast<T*>(v);
+    return s;
+}
+
+void release(asfd_plan_s* P, void* p)
+{
+    for (size_t i = 0; i < P->owned.size(); ++i) {
+        if (P->owned[i].p == p) {
+            P->device_bytes -= P->owned[i].bytes;
+            cudaFree(p);
+            P->owned.erase(P->owned.begin() + i);
+            return;
+        }
+    }
+}
+
+bool pow2_in(int n, int lo, int hi) { return n >= lo && n <= hi && (n & (n - 1)) == 0; }
+
+}  // namespace
+
+asfd_status plan_validate(const asfd_params* p, int* nfx, int* nfy, double* beta)
+{
+    if (!p) return fail(ASFD_ERR_ARG, "params is NULL");
+    auto even_in = [](int n) { return n >= 2 && n <= 65536 && n % 2 == 0; };
+    if (!even_in(p->n1x) || !even_in(p->n1y))
+        return fail(ASFD_ERR_ARG, "n1x and n1y must be even and in [2, 65536]");
+    if (!even_in(p->m2x) || !even_in(p->m2y))
+        return fail(ASFD_ERR_ARG, "m2x and m2y must be even and in [2, 65536]");
+    const double pos[] = {p->p1x, p->p1y, p->p2x, p->p2y, p->lambda, p->z0, p->sigma};
+    for (double v : pos)
+        if (!(std::isfinite(v) && v > 0.0))
+            return fail(ASFD_ERR_ARG, "pitches, wavelength, z0 and sigma must be finite and > 0");
+    if (p->kernel_width < 2 || p->kernel_width > 16)
+        return fail(ASFD_ERR_UNSUPPORTED, "kernel_width must be in [2, 16]");
+    if (p->kind != ASFD_KERNEL_ES)
+        return fail(ASFD_ERR_UNSUPPORTED, "only the ES kernel is available in this plan type");
+    if (!(p->sigma >= 1.25 && p->sigma <= 4.0))
+        return fail(ASFD_ERR_UNSUPPORTED, "sigma must be in [1.25, 4]");
+    const double fx = p->sigma * p->m2x, fy = p->sigma * p->m2y;
+    const int ix = (int)std::lround(fx), iy = (int)std::lround(fy);
+    if (std::fabs(fx - ix) > 1e-9 * fx || std::fabs(fy - iy) > 1e-9 * fy || !pow2_in(ix, 64, 16384) ||
+        !pow2_in(iy, 64, 16384))
+        return fail(ASFD_ERR_UNSUPPORTED,
+                    "sigma*m2x and sigma*m2y must be powers of two in [64, 16384]");
+    if (p->kernel_width >= ix / 2 || p->kernel_width >= iy / 2)
+        return fail(ASFD_ERR_UNSUPPORTED, "kernel wider than half the fine grid");
+    if (!(std::isfinite(p->es_beta) && p->es_beta >= 0.0))
+        return fail(ASFD_ERR_ARG, "es_beta must be finite and >= 0");
+    const double pi = 3.14159265358979323846;
+    double b = p->es_beta;
+    if (b == 0.0)
+        b = (p->sigma == 2.0) ? 2.30 * p->kernel_width
+                              : 0.97 * pi * (1.0 - 1.0 / (2.0 * p->sigma)) * p->kernel_width;
+    *nfx = ix;
+    *nfy = iy;
+    *beta = b;
+    return ASFD_OK;
+}
+
+asfd_status plan_alloc(asfd_plan_s* P)
+{
+    const asfd_params& p = P->prm;
+    const size_t nsrc = (size_t)p.n1x * p.n1y;
+    P->nstx = (p.n1x + kSrcTile - 1) / kSrcTile;
+    P->nsty = (p.n1y + kSrcTile - 1) / kSrcTile;
+    P->ntx = P->nfx / kTileX;
+    P->nty = P->nfy / kTileY;
+    asfd_status s;
+#define A(ptr, n) if ((s = alloc_n(P, &P->ptr, (n))) != ASFD_OK) return s
+    A(ax, p.n1x);
+    A(ay, p.n1y);
+    A(px, p.n1x);
+    A(py, p.n1y);
+    A(bux, p.n1x);
+    A(buy, p.n1y);
+    A(q, nsrc);
+    A(cx, p.m2x);
+    A(cy, p.m2y);
+    A(twx, P->nfx);
+    A(twy, P->nfy);
+    A(src_bbox, (size_t)P->nstx * P->nsty);
+    A(tile_off, (size_t)P->ntx * P->nty + 1);
+    A(grid, (size_t)P->nfx * P->nfy);
+    A(rows, (size_t)P->nfy * p.m2x);
+    A(status, 2);
+#undef A
+    return ASFD_OK;
+}
+
+asfd_status plan_build_tables(asfd_plan_s* P, cudaStream_t st)
+{
+    const asfd_params& p = P->prm;
+    const double lam_z0 = p.lambda * p.z0;
+    P->alpha_x = p.p1x * p.p2x * P->nfx / lam_z0;
+    P->alpha_y = p.p1y * p.p2y * P->nfy / lam_z0;
+    axis_table_kernel<<<(p.n1x + 255) / 256, 256, 0, st>>>(P->ax, P->px, P->bux, p.n1x, p.p1x,
+                                                            lam_z0, P->alpha_x, P->nfx);
+    axis_table_kernel<<<(p.n1y + 255) / 256, 256, 0, st>>>(P->ay, P->py, P->buy, p.n1y, p.p1y,
+                                                            lam_z0, P->alpha_y, P->nfy);
+    ASFD_CUDA(cudaGetLastError());
+
+    // ES kernel values at Gauss-Legendre nodes on [0, w/2]
+    const int nq = 160;
+    std::vector<double> x, wt, h(2 * nq);
+    gauss_legendre(nq, x, wt);
+    const double half = 0.5 * P->w;
+    for (int i = 0; i < nq; ++i) {
+        const double z = 0.5 * half * (x[i] + 1.0);
+        const double u = z / half;
+        const double psi = std::exp(P->beta * (std::sqrt(std::max(0.0, 1.0 - u * u)) - 1.0));
+        h[i] = z;
+        h[nq + i] = 0.5 * half * wt[i] * psi;
+    }
+    if (!P->quad) {
+        asfd_status s = alloc_n(P, &P->quad, 2 * nq);
+        if (s != ASFD_OK) return s;
+    }
+    P->nq = nq;
+    ASFD_CUDA(cudaMemcpyAsync(P->quad, h.data(), sizeof(double) * 2 * nq, cudaMemcpyHostToDevice, st));
+    const double amp = p.p1x * p.p1y / lam_z0;
+    dest_table_kernel<<<(p.m2x + 255) / 256, 256, 0, st>>>(P->cx, p.m2x, p.p2x, lam_z0, P->nfx,
+                                                            P->quad, nq, 0, 0.0, 0.0);
+    dest_table_kernel<<<(p.m2y + 255) / 256, 256, 0, st>>>(P->cy, p.m2y, p.p2y, lam_z0, P->nfy,
+                                                            P->quad, nq, 1, 2.0 * p.z0 / p.lambda,
+                                                            amp);
+    ASFD_CUDA(cudaGetLastError());
+    asfd_status s = build_twiddles(P->twx, P->nfx, st);
+    if (s != ASFD_OK) return s;
+    s = build_twiddles(P->twy, P->nfy, st);
+    if (s != ASFD_OK) return s;
+    // the host vector h must outlive the async copy
+    ASFD_CUDA(cudaStreamSynchronize(st));
+    return ASFD_OK;
+}
+
+asfd_status plan_build_d1(asfd_plan_s* P, const double* d1, cudaStream_t st)
+{
+    const asfd_params& p = P->prm;
+    const size_t nsrc = (size_t)p.n1x * p.n1y;
+    // 1. validate d1 without touching the plan's tables
+    ASFD_CUDA(cudaMemsetAsync(P->status, 0, 2 * sizeof(unsigned), st));
+    d1_check_kernel<<<(unsigned)((nsrc + 255) / 256), 256, 0, st>>>(d1, nsrc, p.z0, P->status,
+                                                                   P->status + 1);
+    ASFD_CUDA(cudaGetLastError());
+    unsigned hs[2] = {0, 0};
+    ASFD_CUDA(cudaMemcpyAsync(hs, P->status, sizeof(hs), cudaMemcpyDeviceToHost, st));
+    ASFD_CUDA(cudaStreamSynchronize(st));
+    if (hs[0] & kStatusBadD1) return fail(ASFD_ERR_ARG, "d1 has a non-finite value or d1 >= z0");
+    float me;
+    std::memcpy(&me, &hs[1], sizeof(float));
+    if (me > 0.1f)
+        return fail(ASFD_ERR_UNSUPPORTED, "max |d1|/z0 = " + std::to_string(me) +
+                                              " exceeds the supported 0.1");
+
+    // 2. per-sample correction and per-source-tile footprint bounds
+    d1_q_kernel<<<(unsigned)((nsrc + 255) / 256), 256, 0, st>>>(d1, P->q, nsrc, p.z0);
+    const int nst = P->nstx * P->nsty;
+    src_bbox_kernel<<<nst, kSrcTile * kSrcTile, 0, st>>>(P->q, P->ax, P->ay, P->bux, P->buy, p.n1x,
+                                                         p.n1y, P->nstx, P->src_bbox);
+    ASFD_CUDA(cudaGetLastError());
+    std::vector<double> bb(4 * (size_t)nst);
+    ASFD_CUDA(cudaMemcpyAsync(bb.data(), P->src_bbox, sizeof(double) * 4 * nst,
+                              cudaMemcpyDeviceToHost, st));
+    ASFD_CUDA(cudaStreamSynchronize(st));
+
+    // 3. host binning: output tile -> list of source tiles (CSR over the band)
+    const double hw = 0.5 * P->w + 1.0;  // half width plus a one-cell safety margin
+    struct Range { int x0, x1, y0, y1; };
+    std::vector<Range> rg(nst);
+    bool wrapx = false, wrapy = false;
+    int bx0 = P->ntx, bx1 = -1, by0 = P->nty, by1 = -1;
+    for (int t = 0; t < nst; ++t) {
+        const double* b = &bb[4 * (size_t)t];
+        Range r;
+        r.x0 = (int)std::floor((b[0] - hw) / kTileX);
+        r.x1 = (int)std::floor((b[1] + hw) / kTileX);
+        r.y0 = (int)std::floor((b[2] - hw) / kTileY);
+        r.y1 = (int)std::floor((b[3] + hw) / kTileY);
+        if (r.x1 - r.x0 + 1 >= P->ntx) { r.x0 = 0; r.x1 = P->ntx - 1; }
+        if (r.y1 - r.y0 + 1 >= P->nty) { r.y0 = 0; r.y1 = P->nty - 1; }
+        if (r.x0 < 0 || r.x1 >= P->ntx) wrapx = true;
+        if (r.y0 < 0 || r.y1 >= P->nty) wrapy = true;
+        bx0 = std::min(bx0, r.x0);
+        bx1 = std::max(bx1, r.x1);
+        by0 = std::min(by0, r.y0);
+        by1 = std::max(by1, r.y1);
+        rg[t] = r;
+    }
+    if (wrapx) { bx0 = 0; bx1 = P->ntx - 1; }
+    if (wrapy) { by0 = 0; by1 = P->nty - 1; }
+    const int bntx = bx1 - bx0 + 1, bnty = by1 - by0 + 1;
+    const int ntiles = bntx * bnty;
+    std::vector<int> off(ntiles + 1, 0);
+    auto tmod = [](int v, int n) { int m = v % n; return m < 0 ? m + n : m; };
+    for (int t = 0; t < nst; ++t) {
+        const Range& r = rg[t];
+        for (int ty = r.y0; ty <= r.y1; ++ty)
+            for (int tx = r.x0; tx <= r.x1; ++tx) {
+                const int i = (tmod(ty, P->nty) - by0) * bntx + (tmod(tx, P->ntx) - bx0);
+                ++off[i + 1];
+            }
+    }
+    for (int i = 0; i < ntiles; ++i) off[i + 1] += off[i];
+    std::vector<int> lst(off[ntiles]);
+    std::vector<int> fillp(off.begin(), off.end() - 1);
+    for (int t = 0; t < nst; ++t) {
+        const Range& r = rg[t];
+        for (int ty = r.y0; ty <= r.y1; ++ty)
+            for (int tx = r.x0; tx <= r.x1; ++tx) {
+                const int i = (tmod(ty, P->nty) - by0) * bntx + (tmod(tx, P->ntx) - bx0);
+                lst[fillp[i]++] = t;
+            }
+    }
+    if (lst.size() > P->tile_src_cap || !P->tile_src) {
+        if (P->tile_src) release(P, P->tile_src);
+        P->tile_src = nullptr;
+        const size_t cap = std::max<size_t>(lst.size() + lst.size() / 4, 1024);
+        asfd_status s = alloc_n(P, &P->tile_src, cap);
+        if (s != ASFD_OK) { P->tile_src_cap = 0; return s; }
+        P->tile_src_cap = cap;
+    }
+    ASFD_CUDA(cudaMemcpyAsync(P->tile_off, off.data(), sizeof(int) * (ntiles + 1),
+                              cudaMemcpyHostToDevice, st));
+    if (!lst.empty())
+        ASFD_CUDA(cudaMemcpyAsync(P->tile_src, lst.data(), sizeof(int) * lst.size(),
+                                  cudaMemcpyHostToDevice, st));
+    ASFD_CUDA(cudaStreamSynchronize(st));
+    P->band_tx0 = bx0;
+    P->band_tx1 = bx1 + 1;
+    P->band_ty0 = by0;
+    P->band_ty1 = by1 + 1;
+    P->tile_pairs = (long long)lst.size();
+    P->max_abs_eps = me;
+    return ASFD_OK;
+}
+
+}  // namespace asfd

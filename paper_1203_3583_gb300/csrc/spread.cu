@@ -1,0 +1,204 @@
+// Per-sample prefactor fused with the tiled type-1 spread (Sec. 2, Eqs. 7-9).
+//
+// Sample n = (nx, ny) carries
+//   c_n = u1[n] * exp(ik d1) * exp(ik(-d1 + |x1|^2/(2 r0)))
+// and sits at the non-uniform frequency t = k p2 x1 / r0 (per axis), i.e. at
+// the fine-grid coordinate g = t nf/(2 pi) = alpha x~ (1 + q), with
+// alpha = p1 p2 nf/(lambda z0), x~ = n - N/2 and q = d1/(z0 - d1).
+//
+// Phase split (the large phases are formed and reduced in FP64 by the plan):
+//   exp(ik d1) exp(-ik d1) = 1 exactly for the normally incident plane wave,
+//   k|x1|^2/(2 r0) = pi a (1 + q),  a = |x1|^2/(lambda z0) = a_x + a_y,
+// so c_n = u1 * E_x[nx] E_y[ny] * exp(i pi (a_x + a_y) q), where the tables
+// E = exp(i pi a) were built and reduced mod 2 pi in FP64 and only the
+// correction pi a q is evaluated per sample, in FP32 with sincospif.  Its
+// absolute error is about 2^-23 (a q + a |q|), e.g. 1e-7 rad at a = 500
+// half-turns and q = 5e-4; it grows linearly with q, which the plan bounds
+// by |d1|/z0 <= 0.1.  Likewise g = (bi + bf) + s q with the FP64-built
+// integer/fraction split of alpha x~ + nf/2 and s = alpha x~, so the FP32
+// error of g is that of the small term s q (about 1e-7 cells at the standard
+// workloads) rather than that of g itself.
+//
+// Each CTA owns one kTileX x kTileY tile of the fine grid (storage
+// coordinates, centred: cell index = g + nf/2 mod nf), accumulates in shared
+// memory the contributions of every sample whose footprint reaches the tile
+// (source tiles listed by the plan's binning), and writes the tile to global
+// memory once.  No global atomics.  The periodic wrap of the fine grid is
+// honoured for every tap.
+#include "asfd_impl.cuh"
+
+namespace asfd {
+
+namespace {
+
+struct SpreadArgs {
+    const float2* u1;
+    const float* q;
+    const AxisEntry* ax;
+    const AxisEntry* ay;
+    const AxisPos* px;
+    const AxisPos* py;
+    const int* tile_off;
+    const int* tile_src;
+    float2* grid;
+    int n1x, n1y;
+    int nfx, nfy;
+    int nstx;
+    int band_tx0, band_ty0, band_ntx;
+    float half_w;      // w/2
+    float beta_log2e;  // beta * log2(e)
+    float two_over_w;  // 2/w
+};
+
+// ES kernel psi(z) = exp(beta (sqrt(1 - (2z/w)^2) - 1)), |z| <= w/2.
+__device__ __forceinline__ float es_weight(float z, float two_over_w, float beta_log2e)
+{
+    const float u = z * two_over_w;
+    const float r = fmaxf(1.0f - u * u, 0.0f);
+    return exp2f(beta_log2e * (sqrtf(r) - 1.0f));
+}
+
+template <int W>
+__global__ void __launch_bounds__(256) spread_es_kernel(SpreadArgs a)
+{
+    __shared__ float tre[kTileY * kTileX];
+    __shared__ float tim[kTileY * kTileX];
+
+    const int tile = blockIdx.x;
+    const int ty = a.band_ty0 + tile / a.band_ntx;
+    const int tx = a.band_tx0 + tile % a.band_ntx;
+    const int ox = tx * kTileX, oy = ty * kTileY;
+
+    for (int i = threadIdx.x; i < kTileX * kTileY; i += blockDim.x) {
+        tre[i] = 0.f;
+        tim[i] = 0.f;
+    }
+    __syncthreads();
+
+    const int beg = a.tile_off[tile], end = a.tile_off[tile + 1];
+    const int total = (end - beg) * (kSrcTile * kSrcTile);
+    const int mx = a.nfx - 1, my = a.nfy - 1;
+    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+        const int s = a.tile_src[beg + idx / (kSrcTile * kSrcTile)];
+        const int local = idx % (kSrcTile * kSrcTile);
+        const int nx = (s % a.nstx) * kSrcTile + local % kSrcTile;
+        const int ny = (s / a.nstx) * kSrcTile + local / kSrcTile;
+        if (nx >= a.n1x || ny >= a.n1y) continue;
+        const size_t n = (size_t)ny * a.n1x + nx;
+        const float q = __ldg(&a.q[n]);
+        const AxisEntry ex = a.ax[nx], ey = a.ay[ny];
+        const AxisPos px = a.px[nx], py = a.py[ny];
+
+        // storage coordinate relative to bi: bf + s q; first tap l0 = bi + ceil(f)
+        const float fx = px.bf + ex.s * q - a.half_w;
+        const float fy = py.bf + ey.s * q - a.half_w;
+        const float cfx = ceilf(fx), cfy = ceilf(fy);
+        const int cx0 = (px.bi + (int)cfx - ox) & mx;  // tile-relative, wrapped to [0, nf)
+        const int cy0 = (py.bi + (int)cfy - oy) & my;
+        const bool hitx = (cx0 < kTileX) || (cx0 + W - 1 > mx);
+        const bool hity = (cy0 < kTileY) || (cy0 + W - 1 > my);
+        if (!(hitx && hity)) continue;
+        const float dx = cfx - fx, dy = cfy - fy;  // in [0, 1)
+
+        // prefactor c = u1 E_x E_y exp(i pi (a_x + a_y) q)
+        float sn, cs;
+        sincospif((ex.a + ey.a) * q, &sn, &cs);
+        const float2 u = __ldg(&a.u1[n]);
+        const float2 exy = make_float2(ex.e.x * ey.e.x - ex.e.y * ey.e.y,
+                                       ex.e.x * ey.e.y + ex.e.y * ey.e.x);
+        const float2 t1 = make_float2(u.x * exy.x - u.y * exy.y, u.x * exy.y + u.y * exy.x);
+        const float2 c = make_float2(t1.x * cs - t1.y * sn, t1.x * sn + t1.y * cs);
+
+        float wx[W];
+#pragma unroll
+        for (int i = 0; i < W; ++i) wx[i] = es_weight(dx + (float)i - a.half_w, a.two_over_w, a.beta_log2e);
+
+#pragma unroll
+        for (int j = 0; j < W; ++j) {
+            int row = cy0 + j;
+            if (row > my) row -= a.nfy;
+            if (row >= kTileY) continue;
+            const float wy = es_weight(dy + (float)j - a.half_w, a.two_over_w, a.beta_log2e);
+            const float cr = c.x * wy, ci = c.y * wy;
+            float* rre = tre + row * kTileX;
+            float* rim = tim + row * kTileX;
+#pragma unroll
+            for (int i = 0; i < W; ++i) {
+                int col = cx0 + i;
+                if (col > mx) col -= a.nfx;
+                if (col >= kTileX) continue;
+                atomicAdd(rre + col, cr * wx[i]);
+                atomicAdd(rim + col, ci * wx[i]);
+            }
+        }
+    }
+    __syncthreads();
+
+    // write the tile (two cells per float4)
+    float4* g4 = reinterpret_cast<float4*>(a.grid);
+    for (int i = threadIdx.x; i < kTileX * kTileY / 2; i += blockDim.x) {
+        const int r = i / (kTileX / 2), c2 = i % (kTileX / 2);
+        const int l = r * kTileX + 2 * c2;
+        const size_t o = ((size_t)(oy + r) * a.nfx + ox) / 2 + c2;
+        g4[o] = make_float4(tre[l], tim[l], tre[l + 1], tim[l + 1]);
+    }
+}
+
+template <int W>
+cudaError_t launch_w(const SpreadArgs& a, int tiles, cudaStream_t st)
+{
+    spread_es_kernel<W><<<tiles, 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+asfd_status launch_spread(asfd_plan_s* P, const float2* u1, cudaStream_t st)
+{
+    SpreadArgs a;
+    a.u1 = u1;
+    a.q = P->q;
+    a.ax = P->ax;
+    a.ay = P->ay;
+    a.px = P->px;
+    a.py = P->py;
+    a.tile_off = P->tile_off;
+    a.tile_src = P->tile_src;
+    a.grid = P->grid;
+    a.n1x = P->prm.n1x;
+    a.n1y = P->prm.n1y;
+    a.nfx = P->nfx;
+    a.nfy = P->nfy;
+    a.nstx = P->nstx;
+    a.band_tx0 = P->band_tx0;
+    a.band_ty0 = P->band_ty0;
+    a.band_ntx = P->band_tx1 - P->band_tx0;
+    a.half_w = 0.5f * (float)P->w;
+    a.beta_log2e = (float)(P->beta * 1.4426950408889634074);
+    a.two_over_w = (float)(2.0 / P->w);
+    const int tiles = (P->band_tx1 - P->band_tx0) * (P->band_ty1 - P->band_ty0);
+    if (tiles <= 0) return ASFD_OK;
+    cudaError_t e;
+    switch (P->w) {
+        case 2: e = launch_w<2>(a, tiles, st); break;
+        case 3: e = launch_w<3>(a, tiles, st); break;
+        case 4: e = launch_w<4>(a, tiles, st); break;
+        case 5: e = launch_w<5>(a, tiles, st); break;
+        case 6: e = launch_w<6>(a, tiles, st); break;
+        case 7: e = launch_w<7>(a, tiles, st); break;
+        case 8: e = launch_w<8>(a, tiles, st); break;
+        case 9: e = launch_w<9>(a, tiles, st); break;
+        case 10: e = launch_w<10>(a, tiles, st); break;
+        case 11: e = launch_w<11>(a, tiles, st); break;
+        case 12: e = launch_w<12>(a, tiles, st); break;
+        case 13: e = launch_w<13>(a, tiles, st); break;
+        case 14: e = launch_w<14>(a, tiles, st); break;
+        case 15: e = launch_w<15>(a, tiles, st); break;
+        case 16: e = launch_w<16>(a, tiles, st); break;
+        default: return fail(ASFD_ERR_UNSUPPORTED, "kernel width outside 2..16");
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "spread_es_kernel launch");
+    return ASFD_OK;
+}
+
+}  // namespace asfd

@@ -1,0 +1,83 @@
+"""High-level handle over the C ABI: one plan per (geometry, height map).
+
+    plan = FresnelPlan(geometry, d1)      # d1: float64 [n1y, n1x] (CUDA tensor or array)
+    u2 = plan.execute(u1)                 # u1: complex64 [n1y, n1x] CUDA tensor
+    plan.close()
+
+All computation happens in libasfd.so on the current CUDA stream; this class
+only owns the plan handle and allocates output tensors through PyTorch.
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import capi
+
+
+def _as_cuda_f64(d1) -> torch.Tensor:
+    if isinstance(d1, torch.Tensor):
+        t = d1.to(device="cuda", dtype=torch.float64)
+    else:
+        t = torch.as_tensor(np.ascontiguousarray(d1, np.float64), device="cuda")
+    return t.contiguous()
+
+
+class FresnelPlan:
+    """Plan for Eq. 8 of the paper on one GPU (see include/asfd.h)."""
+
+    def __init__(self, geometry: dict, d1, sigma: float = 2.0, kernel_width: int = 7,
+                 es_beta: float = 0.0, stream=None):
+        self.geometry = dict(geometry)
+        self.params = capi.make_params(geometry, sigma=sigma, kernel_width=kernel_width,
+                                       es_beta=es_beta)
+        self.shape1 = (int(geometry["n1y"]), int(geometry["n1x"]))
+        self.shape2 = (int(geometry["m2y"]), int(geometry["m2x"]))
+        self._handle = None
+        self._handle = capi.asfd_plan_create(self.params, _as_cuda_f64(d1), stream)
+
+    @property
+    def handle(self):
+        if self._handle is None:
+            raise RuntimeError("plan is closed")
+        return self._handle
+
+    def update_d1(self, d1, stream=None) -> None:
+        capi.asfd_plan_update_d1(self.handle, _as_cuda_f64(d1), self.shape1[1], self.shape1[0],
+                                 stream)
+
+    def execute(self, u1: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        if out is None:
+            out = torch.empty(self.shape2, dtype=torch.complex64, device=u1.device)
+        capi.asfd_execute(self.handle, u1, out, self.shape1, self.shape2, stream)
+        return out
+
+    def execute_stage(self, stage: int, u1=None, out=None, stream=None) -> None:
+        capi.asfd_execute_stage(self.handle, stage, u1, out, self.shape1, self.shape2, stream)
+
+    def execute_host(self, u1: torch.Tensor, out: torch.Tensor, stream=None) -> torch.Tensor:
+        capi.asfd_execute_host(self.handle, u1, out, self.shape1, self.shape2, stream)
+        return out
+
+    def info(self) -> dict:
+        return capi.asfd_get_plan_info(self.handle)
+
+    def check_device_status(self, stream=None) -> None:
+        capi.asfd_check_device_status(self.handle, stream)
+
+    def close(self) -> None:
+        if self._handle is not None:
+            capi.asfd_destroy(self._handle)
+            self._handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

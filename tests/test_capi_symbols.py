@@ -1,0 +1,90 @@
+"""The C-ABI library builds, loads and exports every entry point of include/asfd.h.
+
+CPU only: nothing here launches device work.
+"""
+from __future__ import annotations
+
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADERS = [os.path.join(ROOT, "include", f) for f in sorted(os.listdir(os.path.join(ROOT, "include")))
+           if f.endswith(".h")]
+
+
+def declared_entry_points():
+    names = set()
+    for h in HEADERS:
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"\b(asfd_[a-z0-9_]+)\s*\(", text):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def lib_path():
+    from paper_1203_3583_gb300 import _build
+    return _build.build()
+
+
+def test_header_declares_entry_points():
+    names = declared_entry_points()
+    assert "asfd_plan_create" in names and "asfd_execute" in names and "asfd_destroy" in names
+
+
+def test_library_exports_every_declared_symbol(lib_path):
+    out = subprocess.run(["nm", "-D", "--defined-only", lib_path], capture_output=True, text=True,
+                         check=True).stdout
+    exported = set(re.findall(r"\bT (asfd_[a-z0-9_]+)\b", out))
+    missing = [n for n in declared_entry_points() if n not in exported]
+    assert not missing, f"declared but not exported: {missing}"
+
+
+def test_binding_covers_every_symbol(lib_path):
+    from paper_1203_3583_gb300 import capi
+    lib = capi.load(lib_path)
+    for name in declared_entry_points():
+        assert name in capi.SIGNATURES, f"{name} has no binding"
+        assert hasattr(lib, name)
+
+
+def test_status_strings_without_gpu(lib_path):
+    from paper_1203_3583_gb300 import capi
+    lib = capi.load(lib_path)
+    assert lib.asfd_status_string(0) == b"ok"
+    assert lib.asfd_status_string(1) == b"invalid argument"
+    assert lib.asfd_status_string(99) == b"unknown status"
+
+
+def test_invalid_arguments_rejected_on_host(lib_path):
+    """Validation happens before any device call, so it runs without a GPU."""
+    import ctypes
+    from paper_1203_3583_gb300 import capi
+    lib = capi.load(lib_path)
+    out = ctypes.c_void_p()
+    g = dict(n1x=64, n1y=64, p1x=1e-5, p1y=1e-5, m2x=64, m2y=64, p2x=1e-5, p2y=1e-5,
+             lam=633e-9, z0=0.05)
+    bad = [
+        dict(g, n1x=63),                     # odd size
+        dict(g, m2x=0),                      # empty
+        dict(g, lam=float("nan")),           # non-finite
+        dict(g, z0=-1.0),                    # negative distance
+    ]
+    for b in bad:
+        p = capi.make_params(b)
+        rc = lib.asfd_plan_create(ctypes.byref(out), ctypes.byref(p), ctypes.c_void_p(1), None)
+        assert rc == 1, (b, rc)
+        assert out.value is None
+    # sigma * m2 not a power of two -> unsupported
+    p = capi.make_params(dict(g, m2x=48))
+    assert lib.asfd_plan_create(ctypes.byref(out), ctypes.byref(p), ctypes.c_void_p(1), None) == 5
+    p = capi.make_params(g, kernel_width=17)
+    assert lib.asfd_plan_create(ctypes.byref(out), ctypes.byref(p), ctypes.c_void_p(1), None) == 5
+    # NULL d1
+    p = capi.make_params(g)
+    assert lib.asfd_plan_create(ctypes.byref(out), ctypes.byref(p), None, None) == 1
+    assert b"NULL" in lib.asfd_last_error()

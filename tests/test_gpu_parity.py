@@ -1,0 +1,224 @@
+"""CUDA path against the FP64 oracle (discretised Eq. 7), through the C ABI.
+
+Tolerance: relative L2 error <= 1e-5 for the exponential-of-semicircle kernel
+at width 7 and oversampling 2 (the accuracy target of the plain method).
+Small cases compare every destination point; the full-size workloads compare
+seeded random destination points (the oracle is O(N^2) per point), and the
+constant-height case compares the full 1024^2 grid against the separable FP64
+form that Eq. 7 takes when d1 is constant.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle  # noqa: E402
+from paper_1203_3583_gb300 import capi, workloads as W  # noqa: E402
+from paper_1203_3583_gb300.fresnel import FresnelPlan  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+TOL_ES = 1e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1203_3583_gb300 import _build
+    capi.load(_build.build())
+
+
+def rel_l2(a, b):
+    a = np.asarray(a, np.complex128).ravel()
+    b = np.asarray(b, np.complex128).ravel()
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def run_gpu(g, u1, d1, **kw):
+    with FresnelPlan(g, d1, **kw) as plan:
+        u2 = plan.execute(torch.as_tensor(u1, device="cuda"))
+        torch.cuda.synchronize()
+        plan.check_device_status()
+        return u2.cpu().numpy(), plan.info()
+
+
+# --- the FFT kernel on its own ------------------------------------------------------
+
+@pytest.mark.parametrize("n", [16, 32, 64, 128, 256, 512, 1024, 2048, 4096, 8192, 16384])
+@pytest.mark.parametrize("sign", [-1, 1])
+def test_fft_lines_against_numpy(n, sign):
+    rng = np.random.default_rng(n + (sign > 0))
+    lines = 37
+    x = (rng.standard_normal((lines, n)) + 1j * rng.standard_normal((lines, n))).astype(np.complex64)
+    y = capi.asfd_fft_lines(torch.as_tensor(x, device="cuda"), sign=sign)
+    torch.cuda.synchronize()
+    ref = np.fft.fft(x.astype(np.complex128), axis=1) if sign < 0 else \
+        np.fft.ifft(x.astype(np.complex128), axis=1) * n
+    err = rel_l2(y.cpu().numpy(), ref)
+    assert err < 1e-6, f"n={n} sign={sign}: {err:.2e}"
+
+
+def test_fft_lines_in_place():
+    rng = np.random.default_rng(5)
+    x = (rng.standard_normal((9, 4096)) + 1j * rng.standard_normal((9, 4096))).astype(np.complex64)
+    t = torch.as_tensor(x, device="cuda")
+    capi.asfd_fft_lines(t, sign=-1, out=t)
+    torch.cuda.synchronize()
+    assert rel_l2(t.cpu().numpy(), np.fft.fft(x.astype(np.complex128), axis=1)) < 1e-6
+
+
+# --- the whole transform -------------------------------------------------------------
+
+def test_sinusoid64_full_grid():
+    g, u1, d1 = W.make("sinusoid64")
+    out, _ = run_gpu(g, u1, d1)
+    ref = oracle.eq7(g, u1, d1)
+    err = rel_l2(out, ref)
+    assert err < TOL_ES, err
+
+
+def test_ragged_nonsquare_full_grid():
+    """Source sizes not a multiple of the 16-sample binning tile, unequal pitches
+    and sizes per axis, destination smaller than source, asymmetric field."""
+    rng = np.random.default_rng(21)
+    g = W.geometry(50, 38, 10e-6, 7e-6, 64, 32, 12e-6, 9e-6, 532e-9, 0.04)
+    u1 = (rng.standard_normal((38, 50)) + 1j * rng.standard_normal((38, 50))).astype(np.complex64)
+    d1 = W.surface_smooth_random(g, rng, 4.0, 60e-6) - 30e-6
+    out, _ = run_gpu(g, u1, d1)
+    err = rel_l2(out, oracle.eq7(g, u1, d1))
+    assert err < TOL_ES, err
+
+
+def test_periodic_wrap_full_grid():
+    """Samples whose frequency t exceeds pi: positions wrap around the fine grid
+    several times (the sum is 2 pi periodic in t)."""
+    rng = np.random.default_rng(22)
+    g = W.geometry(64, 64, 20e-6, 20e-6, 64, 64, 20e-6, 20e-6, 633e-9, 0.02)
+    u1 = (rng.standard_normal((64, 64)) + 1j * rng.standard_normal((64, 64))).astype(np.complex64)
+    d1 = W.surface_sinusoid(g, 40e-6, 400e-6)
+    out, info = run_gpu(g, u1, d1)
+    assert info["band_x0"] == 0 and info["band_x1"] == info["nfx"]
+    err = rel_l2(out, oracle.eq7(g, u1, d1))
+    assert err < TOL_ES, err
+
+
+def test_zero_field_gives_zero():
+    g, u1, d1 = W.make("sinusoid64")
+    out, _ = run_gpu(g, np.zeros_like(u1), d1)
+    assert np.all(out == 0)
+
+
+def test_single_sample():
+    g, _, d1 = W.make("sinusoid64")
+    u1 = np.zeros((64, 64), np.complex64)
+    u1[17, 40] = 0.5 - 0.25j
+    out, _ = run_gpu(g, u1, d1)
+    assert rel_l2(out, oracle.eq7(g, u1, d1)) < TOL_ES
+
+
+@pytest.mark.parametrize("width", [4, 5, 6, 7, 8, 10, 12])
+def test_kernel_width_accuracy(width):
+    """ES error falls roughly tenfold per unit of width until FP32 rounding."""
+    g, u1, d1 = W.make("sinusoid64")
+    rng = np.random.default_rng(23)
+    u1 = (rng.standard_normal((64, 64)) + 1j * rng.standard_normal((64, 64))).astype(np.complex64)
+    out, _ = run_gpu(g, u1, d1, kernel_width=width)
+    err = rel_l2(out, oracle.eq7(g, u1, d1))
+    bound = max(3.0 * 10.0 ** (-(width - 1)), 2e-6)
+    assert err < bound, (width, err)
+
+
+def test_spherical_cap1024_sampled():
+    g, u1, d1 = W.make("spherical_cap1024")
+    pts = W.sample_points(g, 4096, seed=102)
+    out, _ = run_gpu(g, u1, d1)
+    ref = oracle.eq7(g, u1, d1, points=pts)
+    err = rel_l2(out[pts[1], pts[0]], ref)
+    assert err < TOL_ES, err
+
+
+def test_smooth_random2048_sampled():
+    g, u1, d1 = W.make("smooth_random2048")
+    pts = W.sample_points(g, 1024, seed=103)
+    out, _ = run_gpu(g, u1, d1)
+    ref = oracle.eq7(g, u1, d1, points=pts)
+    err = rel_l2(out[pts[1], pts[0]], ref)
+    assert err < TOL_ES, err
+
+
+def test_tilt_bump4096_sampled():
+    g, u1, d1 = W.make("tilt_bump4096")
+    pts = W.sample_points(g, 256, seed=105)
+    out, _ = run_gpu(g, u1, d1)
+    ref = oracle.eq7(g, u1, d1, points=pts)
+    err = rel_l2(out[pts[1], pts[0]], ref)
+    assert err < TOL_ES, err
+
+
+def test_constant_height_full_grid_1024():
+    """d1 = c: Eq. 7 factorises into Ey (u1 o chirp) Ex^T with 1D FP64 DFT
+    matrices at distance r0 = z0 - c; compared over the full 1024^2 grid."""
+    g, u1, _ = W.make("spherical_cap1024")
+    c = 0.4e-3
+    d1 = np.full((g["n1y"], g["n1x"]), c)
+    out, _ = run_gpu(g, u1, d1)
+    k = 2 * np.pi / g["lam"]
+    r0 = g["z0"] - c
+    x1 = W.coords(g["n1x"], g["p1x"])
+    y1 = W.coords(g["n1y"], g["p1y"])
+    x2 = W.coords(g["m2x"], g["p2x"])
+    y2 = W.coords(g["m2y"], g["p2y"])
+    ex = np.exp(-1j * k * np.outer(x2, x1) / r0)
+    ey = np.exp(-1j * k * np.outer(y2, y1) / r0)
+    f = u1.astype(np.complex128) * np.outer(np.exp(1j * k * y1 ** 2 / (2 * r0)),
+                                            np.exp(1j * k * x1 ** 2 / (2 * r0)))
+    s = ey @ f @ ex.T
+    outer = np.exp(1j * k * (g["z0"] + (x2[None, :] ** 2 + y2[:, None] ** 2) / (2 * g["z0"]))) / (
+        1j * g["lam"] * g["z0"])
+    ref = outer * g["p1x"] * g["p1y"] * s
+    # spot-check the separable reference against the oracle itself
+    pts = W.sample_points(g, 64, seed=104)
+    assert rel_l2(ref[pts[1], pts[0]], oracle.eq7(g, u1, d1, points=pts)) < 1e-9
+    err = rel_l2(out, ref)
+    assert err < TOL_ES, err
+
+
+def test_execute_host_matches_device():
+    g, u1, d1 = W.make("sinusoid64")
+    with FresnelPlan(g, d1) as plan:
+        dev = plan.execute(torch.as_tensor(u1, device="cuda")).cpu().numpy()
+        hu1 = torch.as_tensor(u1).pin_memory()
+        hu2 = torch.empty((64, 64), dtype=torch.complex64).pin_memory()
+        plan.execute_host(hu1, hu2)
+        assert rel_l2(hu2.numpy(), dev) < 1e-6
+
+
+def test_update_d1_equals_fresh_plan():
+    g, u1, d1 = W.make("sinusoid64")
+    d1b = -0.5 * d1 + 5e-6
+    u1t = torch.as_tensor(u1, device="cuda")
+    with FresnelPlan(g, d1) as plan:
+        plan.update_d1(d1b)
+        a = plan.execute(u1t).cpu().numpy()
+    with FresnelPlan(g, d1b) as plan:
+        b = plan.execute(u1t).cpu().numpy()
+    assert rel_l2(a, b) < 1e-6
+    assert rel_l2(a, oracle.eq7(g, u1, d1b)) < TOL_ES
+
+
+@pytest.mark.parametrize("bad,status", [("nan", 1), ("above_z0", 1), ("too_tall", 5)])
+def test_invalid_height_map_rejected(bad, status):
+    g, _, d1 = W.make("sinusoid64")
+    d1 = d1.copy()
+    if bad == "nan":
+        d1[3, 4] = np.nan
+    elif bad == "above_z0":
+        d1[10, 10] = g["z0"] * 1.01
+    else:
+        d1[10, 10] = 0.2 * g["z0"]
+    with pytest.raises(capi.AsfdError) as ei:
+        FresnelPlan(g, d1)
+    assert ei.value.status == status
