@@ -39,7 +39,7 @@ FALLBACK_HBM_GBS = 6800.0
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--width", type=int, default=7)
@@ -73,16 +73,25 @@ class ClockSampler:
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index: int):
+    def __init__(self, gpu_index: int, interval_ms: int = 50):
         self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
         self.proc = None
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", str(interval_ms)],
                 stdout=self.file, stderr=subprocess.DEVNULL)
         except (OSError, ValueError):
             self.proc = None
+
+    def wait_first_sample(self, timeout_s: float = 5.0):
+        """Block until nvidia-smi has written a line (it needs ~0.1-1 s to start)."""
+        t = time.perf_counter()
+        while self.proc is not None and time.perf_counter() - t < timeout_s:
+            self.file.flush()
+            if os.path.getsize(self.file.name) > 0:
+                return
+            time.sleep(0.02)
 
     def stop(self):
         if self.proc is None:
@@ -113,7 +122,7 @@ class ClockSampler:
         if not sm:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "window": "warm-up + timed region"}
 
 
 def measured_peaks():
@@ -234,6 +243,11 @@ def run_ours(args):
         plan.execute_stage(2, out=u2_d)
         ev[3].record(stream)
 
+    # clocks are sampled from the start of the warm-up to the end of the timed
+    # region (the timed region alone is often shorter than one sample period)
+    clocks = ClockSampler(local) if rank == 0 else None
+    if clocks:
+        clocks.wait_first_sample()
     for _ in range(args.warmup):
         flush.zero_()
         step([torch.cuda.Event(enable_timing=True) for _ in range(4)])
@@ -244,7 +258,6 @@ def run_ours(args):
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    clocks = ClockSampler(local) if rank == 0 else None
     wall0 = time.perf_counter()
     for i in range(args.steps):
         flush.zero_()

@@ -84,6 +84,10 @@ typedef struct {
     double es_beta;          /* ES beta in use                                          */
     double max_abs_eps;      /* max |d1| / z0 over the surface                          */
     size_t device_bytes;     /* device memory owned by the plan                         */
+    int spread_kind;         /* 0: conflict-free warp tiles (no atomics) -- used when   */
+                             /*    the map n -> g is monotone with positive spacing and */
+                             /*    no footprint wraps; 1: shared-memory atomics         */
+    int stride_x, stride_y;  /* sample strides between lanes of one warp step (kind 0)  */
 } asfd_plan_info;
 
 /*

@@ -64,6 +64,8 @@ class PlanInfo(ctypes.Structure):
         ("es_beta", ctypes.c_double),
         ("max_abs_eps", ctypes.c_double),
         ("device_bytes", ctypes.c_size_t),
+        ("spread_kind", ctypes.c_int),
+        ("stride_x", ctypes.c_int), ("stride_y", ctypes.c_int),
     ]
 
 

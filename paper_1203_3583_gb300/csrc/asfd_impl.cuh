@@ -17,6 +17,7 @@ namespace asfd {
 constexpr int kTileX = 64;
 constexpr int kTileY = 64;
 constexpr int kSrcTile = 16;  // source tiles are kSrcTile x kSrcTile samples
+constexpr int kColTileY = 32; // rows of a tile of the conflict-free spreading kernel
 
 // Device status word bits (set by kernels, read by asfd_check_device_status).
 constexpr unsigned kStatusBadD1 = 1u;       // non-finite d1 or d1 >= z0
@@ -78,6 +79,16 @@ struct asfd_plan_s {
     int* tile_off = nullptr;        // [band tiles + 1] CSR offsets
     int* tile_src = nullptr;        // CSR source-tile ids
     int band_tx0 = 0, band_tx1 = 0, band_ty0 = 0, band_ty1 = 0;  // band in tiles
+    // conflict-free ("colored") spreading: per band tile the rectangle of
+    // source samples whose footprints can reach it, and the minimum column
+    // and row strides between samples handled in the same warp step
+    int4* tile_rect = nullptr;      // per kTileX x kColTileY tile of the band
+    double2* col_range = nullptr;   // per source column: [min, max] of the x storage coordinate
+    double2* row_range = nullptr;   // per source row:    [min, max] of the y storage coordinate
+    float2* step_min = nullptr;     // per block of min_step_kernel: min spacing along x and y
+    bool colored = false;
+    int sx_min = 0, h_min = 0;
+    double min_step_x = 0.0, min_step_y = 0.0, row_spread_y = 0.0;
     long long tile_pairs = 0;
     size_t tile_src_cap = 0;
 

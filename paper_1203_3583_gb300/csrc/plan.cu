@@ -147,6 +147,99 @@ __global__ void src_bbox_kernel(const float* q, const AxisEntry* ax, const AxisE
     }
 }
 
+// Per source column: [min, max] over rows of the unreduced x storage coordinate.
+__global__ void col_range_kernel(const float* q, const AxisEntry* ax, const double* bux, int n1x,
+                                 int n1y, double2* out)
+{
+    const int nx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (nx >= n1x) return;
+    const double b = bux[nx];
+    const float s = ax[nx].s;
+    double lo = 1e300, hi = -1e300;
+    for (int ny = 0; ny < n1y; ++ny) {
+        const double g = b + (double)(s * q[(size_t)ny * n1x + nx]);
+        lo = fmin(lo, g);
+        hi = fmax(hi, g);
+    }
+    out[nx] = make_double2(lo, hi);
+}
+
+// Per source row: [min, max] over columns of the unreduced y storage coordinate.
+__global__ void row_range_kernel(const float* q, const AxisEntry* ay, const double* buy, int n1x,
+                                 double2* out)
+{
+    const int ny = blockIdx.x;
+    const double b = buy[ny];
+    const float s = ay[ny].s;
+    double lo = 1e300, hi = -1e300;
+    for (int nx = threadIdx.x; nx < n1x; nx += blockDim.x) {
+        const double g = b + (double)(s * q[(size_t)ny * n1x + nx]);
+        lo = fmin(lo, g);
+        hi = fmax(hi, g);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    __shared__ double red[2][32];
+    if ((threadIdx.x & 31) == 0) {
+        red[0][threadIdx.x / 32] = lo;
+        red[1][threadIdx.x / 32] = hi;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x / 32); ++w) {
+            lo = fmin(lo, red[0][w]);
+            hi = fmax(hi, red[1][w]);
+        }
+        out[ny] = make_double2(lo, hi);
+    }
+}
+
+// Minimum spacing on the fine grid of neighbouring samples: along x within a
+// row and along y within a column (one pair of minima per block).
+__global__ void min_step_kernel(const float* q, const AxisEntry* ax, const AxisEntry* ay,
+                                const double* bux, const double* buy, int n1x, int n1y,
+                                float2* out)
+{
+    const size_t total = (size_t)n1x * n1y;
+    float mx = 3.0e38f, my = 3.0e38f;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const int nx = (int)(i % n1x), ny = (int)(i / n1x);
+        const float qq = q[i];
+        if (nx + 1 < n1x) {
+            const double g0 = bux[nx] + (double)(ax[nx].s * qq);
+            const double g1 = bux[nx + 1] + (double)(ax[nx + 1].s * q[i + 1]);
+            mx = fminf(mx, (float)(g1 - g0));
+        }
+        if (ny + 1 < n1y) {
+            const double g0 = buy[ny] + (double)(ay[ny].s * qq);
+            const double g1 = buy[ny + 1] + (double)(ay[ny + 1].s * q[i + n1x]);
+            my = fminf(my, (float)(g1 - g0));
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        mx = fminf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        my = fminf(my, __shfl_xor_sync(0xffffffffu, my, o));
+    }
+    __shared__ float red[2][32];
+    if ((threadIdx.x & 31) == 0) {
+        red[0][threadIdx.x / 32] = mx;
+        red[1][threadIdx.x / 32] = my;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x / 32); ++w) {
+            mx = fminf(mx, red[0][w]);
+            my = fminf(my, red[1][w]);
+        }
+        out[blockIdx.x] = make_float2(mx, my);
+    }
+}
+
+constexpr int kStepBlocks = 1024;
+
 // Gauss-Legendre nodes and weights on [-1, 1] (Newton iteration on P_n).
 void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& wt)
 {
@@ -222,6 +315,8 @@ bool pow2_in(int n, int lo, int hi) { return n >= lo && n <= hi && (n & (n - 1))
 
 }  // namespace
 
+asfd_status plan_build_colored(asfd_plan_s* P, bool wraps, cudaStream_t st);
+
 asfd_status plan_validate(const asfd_params* p, int* nfx, int* nfy, double* beta)
 {
     if (!p) return fail(ASFD_ERR_ARG, "params is NULL");
@@ -284,6 +379,10 @@ asfd_status plan_alloc(asfd_plan_s* P)
     A(twy, P->nfy);
     A(src_bbox, (size_t)P->nstx * P->nsty);
     A(tile_off, (size_t)P->ntx * P->nty + 1);
+    A(tile_rect, (size_t)P->ntx * P->nty * (kTileY / kColTileY));
+    A(col_range, p.n1x);
+    A(row_range, p.n1y);
+    A(step_min, kStepBlocks);
     A(grid, (size_t)P->nfx * P->nfy);
     A(rows, (size_t)P->nfy * p.m2x);
     A(status, 2);
@@ -435,6 +534,96 @@ asfd_status plan_build_d1(asfd_plan_s* P, const double* d1, cudaStream_t st)
     P->band_ty1 = by1 + 1;
     P->tile_pairs = (long long)lst.size();
     P->max_abs_eps = me;
+    return plan_build_colored(P, wrapx || wrapy, st);
+}
+
+// Decides whether the conflict-free spreading kernel applies and, if so,
+// builds its per-tile source rectangles.  Samples handled in one warp step
+// must have disjoint footprints: two samples of one row `sx` columns apart
+// are at least sx * min_step_x cells apart, two samples `h` rows apart (any
+// columns) at least h * min_step_y - row_spread_y, where row_spread_y bounds
+// the variation of the y coordinate along a row.  Both distances must reach
+// the kernel width (plus a margin for FP32 rounding of the coordinates).
+asfd_status plan_build_colored(asfd_plan_s* P, bool wraps, cudaStream_t st)
+{
+    const asfd_params& p = P->prm;
+    P->colored = false;
+    col_range_kernel<<<(p.n1x + 127) / 128, 128, 0, st>>>(P->q, P->ax, P->bux, p.n1x, p.n1y,
+                                                           P->col_range);
+    row_range_kernel<<<p.n1y, 256, 0, st>>>(P->q, P->ay, P->buy, p.n1x, P->row_range);
+    min_step_kernel<<<kStepBlocks, 256, 0, st>>>(P->q, P->ax, P->ay, P->bux, P->buy, p.n1x, p.n1y,
+                                                 P->step_min);
+    ASFD_CUDA(cudaGetLastError());
+    std::vector<double> cr(2 * (size_t)p.n1x), rr(2 * (size_t)p.n1y);
+    std::vector<float> sm(2 * kStepBlocks);
+    ASFD_CUDA(cudaMemcpyAsync(cr.data(), P->col_range, sizeof(double) * cr.size(),
+                              cudaMemcpyDeviceToHost, st));
+    ASFD_CUDA(cudaMemcpyAsync(rr.data(), P->row_range, sizeof(double) * rr.size(),
+                              cudaMemcpyDeviceToHost, st));
+    ASFD_CUDA(cudaMemcpyAsync(sm.data(), P->step_min, sizeof(float) * sm.size(),
+                              cudaMemcpyDeviceToHost, st));
+    ASFD_CUDA(cudaStreamSynchronize(st));
+    double msx = 3e38, msy = 3e38, spread_y = 0.0;
+    for (int b = 0; b < kStepBlocks; ++b) {
+        msx = std::min(msx, (double)sm[2 * b]);
+        msy = std::min(msy, (double)sm[2 * b + 1]);
+    }
+    for (int ny = 0; ny < p.n1y; ++ny) spread_y = std::max(spread_y, rr[2 * ny + 1] - rr[2 * ny]);
+    if (p.n1x < 2) msx = 1e30;
+    if (p.n1y < 2) msy = 1e30;
+    P->min_step_x = msx;
+    P->min_step_y = msy;
+    P->row_spread_y = spread_y;
+    const double margin = 0.01;
+    if (wraps || !(msx > 0.0) || !(msy > 0.0)) return ASFD_OK;
+    const double sxd = std::ceil((P->w + margin) / msx);
+    const double hd = std::ceil((P->w + spread_y + margin) / msy);
+    if (!(sxd <= 256.0) || !(hd <= 256.0)) return ASFD_OK;
+
+    // per band tile: source columns whose x range meets the tile's x range
+    // widened by half a kernel and a cell, likewise rows (ranges are
+    // monotone in the index because the spacing is positive)
+    const double hw = 0.5 * P->w + 1.0;
+    const int bntx = P->band_tx1 - P->band_tx0;
+    const int bnty = (P->band_ty1 - P->band_ty0) * (kTileY / kColTileY);
+    std::vector<int> xlo(bntx), xhi(bntx), ylo(bnty), yhi(bnty);
+    auto first_hi_ge = [](const std::vector<double>& r, int n, double v) {
+        int lo = 0, hi = n;  // first i with r[2i+1] >= v
+        while (lo < hi) {
+            const int mid = (lo + hi) / 2;
+            if (r[2 * mid + 1] >= v) hi = mid; else lo = mid + 1;
+        }
+        return lo;
+    };
+    auto first_lo_ge = [](const std::vector<double>& r, int n, double v) {
+        int lo = 0, hi = n;  // first i with r[2i] >= v
+        while (lo < hi) {
+            const int mid = (lo + hi) / 2;
+            if (r[2 * mid] >= v) hi = mid; else lo = mid + 1;
+        }
+        return lo;
+    };
+    for (int i = 0; i < bntx; ++i) {
+        const double o = (double)(P->band_tx0 + i) * kTileX;
+        xlo[i] = first_hi_ge(cr, p.n1x, o - hw);
+        xhi[i] = first_lo_ge(cr, p.n1x, o + kTileX + hw);
+    }
+    for (int i = 0; i < bnty; ++i) {
+        const double o = (double)P->band_ty0 * kTileY + (double)i * kColTileY;
+        ylo[i] = first_hi_ge(rr, p.n1y, o - hw);
+        yhi[i] = first_lo_ge(rr, p.n1y, o + kColTileY + hw);
+    }
+    std::vector<int4> rect((size_t)bntx * bnty);
+    for (int j = 0; j < bnty; ++j)
+        for (int i = 0; i < bntx; ++i)
+            rect[(size_t)j * bntx + i] = make_int4(xlo[i], std::max(xlo[i], xhi[i]), ylo[j],
+                                                   std::max(ylo[j], yhi[j]));
+    ASFD_CUDA(cudaMemcpyAsync(P->tile_rect, rect.data(), sizeof(int4) * rect.size(),
+                              cudaMemcpyHostToDevice, st));
+    ASFD_CUDA(cudaStreamSynchronize(st));
+    P->sx_min = (int)sxd;
+    P->h_min = (int)hd;
+    P->colored = true;
     return ASFD_OK;
 }
 

@@ -19,12 +19,21 @@
 // error of g is that of the small term s q (about 1e-7 cells at the standard
 // workloads) rather than that of g itself.
 //
-// Each CTA owns one kTileX x kTileY tile of the fine grid (storage
-// coordinates, centred: cell index = g + nf/2 mod nf), accumulates in shared
-// memory the contributions of every sample whose footprint reaches the tile
-// (source tiles listed by the plan's binning), and writes the tile to global
-// memory once.  No global atomics.  The periodic wrap of the fine grid is
-// honoured for every tap.
+// Both kernels own fine-grid tiles (storage coordinates, centred: cell index
+// = g + nf/2 mod nf): each CTA accumulates in shared memory every tap of
+// every sample whose footprint reaches its tile, and writes the tile to
+// global memory once.  No global atomics.
+//
+//  * spread_es_colored_kernel (the fast path): one warp per tile, plain
+//    shared-memory read-modify-write without atomics.  The plan proves that
+//    the footprints of the 32 samples a warp handles in one step are
+//    pairwise disjoint: lanes form 4 row groups x 8 column groups; lanes of
+//    one row group take samples of the same source row at least Sx columns
+//    apart, row groups take rows at least H apart, where Sx and H follow from
+//    the minimum spacing of the samples on the fine grid (the map n -> g is
+//    monotone for a non-folding surface).  A __syncwarp separates steps.
+//  * spread_es_atomic_kernel (fallback for folding or wrapping maps):
+//    256 threads, one sample per thread, shared-memory atomics.
 #include "asfd_impl.cuh"
 
 namespace asfd {
@@ -40,11 +49,13 @@ struct SpreadArgs {
     const AxisPos* py;
     const int* tile_off;
     const int* tile_src;
+    const int4* tile_rect;
     float2* grid;
     int n1x, n1y;
     int nfx, nfy;
     int nstx;
     int band_tx0, band_ty0, band_ntx;
+    int sx_min, h_min;
     float half_w;      // w/2
     float beta_log2e;  // beta * log2(e)
     float two_over_w;  // 2/w
@@ -55,11 +66,120 @@ __device__ __forceinline__ float es_weight(float z, float two_over_w, float beta
 {
     const float u = z * two_over_w;
     const float r = fmaxf(1.0f - u * u, 0.0f);
-    return exp2f(beta_log2e * (sqrtf(r) - 1.0f));
+    const float s = r > 0.0f ? r * rsqrtf(r) : 0.0f;
+    return exp2f(beta_log2e * (s - 1.0f));
+}
+
+// First tap (storage coordinates, not wrapped) and fractional offset of a sample.
+__device__ __forceinline__ void sample_pos(const AxisEntry& ex, const AxisEntry& ey,
+                                           const AxisPos& px, const AxisPos& py, float q,
+                                           float half_w, int& l0x, int& l0y, float& dx, float& dy)
+{
+    const float fx = px.bf + ex.s * q - half_w;
+    const float fy = py.bf + ey.s * q - half_w;
+    const float cfx = ceilf(fx), cfy = ceilf(fy);
+    l0x = px.bi + (int)cfx;
+    l0y = py.bi + (int)cfy;
+    dx = cfx - fx;  // in [0, 1): tap i sits at dx + i - w/2 from the sample
+    dy = cfy - fy;
+}
+
+// c = u1 E_x E_y exp(i pi (a_x + a_y) q)
+__device__ __forceinline__ float2 sample_value(float2 u, const AxisEntry& ex, const AxisEntry& ey,
+                                               float q)
+{
+    float sn, cs;
+    sincospif((ex.a + ey.a) * q, &sn, &cs);
+    const float2 exy = make_float2(ex.e.x * ey.e.x - ex.e.y * ey.e.y,
+                                   ex.e.x * ey.e.y + ex.e.y * ey.e.x);
+    const float2 t1 = make_float2(u.x * exy.x - u.y * exy.y, u.x * exy.y + u.y * exy.x);
+    return make_float2(t1.x * cs - t1.y * sn, t1.x * sn + t1.y * cs);
+}
+
+// acc + v * w on a complex pair (packed FP32x2 FMA)
+__device__ __forceinline__ float2 fma2(float2 v, float w, float2 acc)
+{
+    unsigned long long r;
+    const unsigned long long vv = *reinterpret_cast<const unsigned long long*>(&v);
+    const unsigned long long aa = *reinterpret_cast<const unsigned long long*>(&acc);
+    const float2 ww = make_float2(w, w);
+    const unsigned long long wb = *reinterpret_cast<const unsigned long long*>(&ww);
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(vv), "l"(wb), "l"(aa));
+    return *reinterpret_cast<float2*>(&r);
+}
+
+template <int W, int TX, int TY>
+__global__ void __launch_bounds__(32) spread_es_colored_kernel(SpreadArgs a)
+{
+    constexpr int LD = TX + 4;  // padded row stride (complex slots)
+    __shared__ __align__(16) float2 tile[TY * LD];
+
+    const int t = blockIdx.x;
+    const int ox = (a.band_tx0 + t % a.band_ntx) * TX;
+    const int oy = a.band_ty0 * kTileY + (t / a.band_ntx) * TY;
+    const int lane = threadIdx.x;
+
+    for (int i = lane; i < TY * LD; i += 32) tile[i] = make_float2(0.f, 0.f);
+    __syncwarp();
+
+    const int4 rc = a.tile_rect[t];  // [x, y) columns, [z, w) rows of source samples
+    const int rw = rc.y - rc.x, rh = rc.w - rc.z;
+    if (rw > 0 && rh > 0) {
+        const int lc = lane & 7, lr = lane >> 3;
+        const int sx = max(a.sx_min, (rw + 7) / 8);
+        const int h = max(a.h_min, (rh + 3) / 4);
+        for (int j = 0; j < h; ++j) {
+            const int ny = rc.z + lr * h + j;
+            for (int o = 0; o < sx; ++o) {
+                const int nx = rc.x + lc * sx + o;
+                if (nx < rc.y && ny < rc.w) {
+                    const size_t n = (size_t)ny * a.n1x + nx;
+                    const float q = __ldg(&a.q[n]);
+                    const AxisEntry ex = a.ax[nx], ey = a.ay[ny];
+                    const AxisPos px = a.px[nx], py = a.py[ny];
+                    int l0x, l0y;
+                    float dx, dy;
+                    sample_pos(ex, ey, px, py, q, a.half_w, l0x, l0y, dx, dy);
+                    const int cx = l0x - ox, cy = l0y - oy;
+                    if (cx > -W && cx < TX && cy > -W && cy < TY) {
+                        const float2 c = sample_value(__ldg(&a.u1[n]), ex, ey, q);
+                        float wx[W];
+#pragma unroll
+                        for (int i = 0; i < W; ++i)
+                            wx[i] = es_weight(dx + (float)i - a.half_w, a.two_over_w, a.beta_log2e);
+#pragma unroll
+                        for (int b = 0; b < W; ++b) {
+                            const int row = cy + b;
+                            if (row < 0 || row >= TY) continue;
+                            const float wy = es_weight(dy + (float)b - a.half_w, a.two_over_w,
+                                                       a.beta_log2e);
+                            const float2 cb = make_float2(c.x * wy, c.y * wy);
+                            float2* tr = tile + row * LD;
+#pragma unroll
+                            for (int i = 0; i < W; ++i) {
+                                const int col = cx + i;
+                                if (col < 0 || col >= TX) continue;
+                                tr[col] = fma2(cb, wx[i], tr[col]);
+                            }
+                        }
+                    }
+                }
+                __syncwarp();
+            }
+        }
+    }
+    __syncwarp();
+
+    float4* g4 = reinterpret_cast<float4*>(a.grid);
+    for (int i = lane; i < TY * (TX / 2); i += 32) {
+        const int r = i / (TX / 2), c2 = i % (TX / 2);
+        const float2 v0 = tile[r * LD + 2 * c2], v1 = tile[r * LD + 2 * c2 + 1];
+        g4[((size_t)(oy + r) * a.nfx + ox) / 2 + c2] = make_float4(v0.x, v0.y, v1.x, v1.y);
+    }
 }
 
 template <int W>
-__global__ void __launch_bounds__(256) spread_es_kernel(SpreadArgs a)
+__global__ void __launch_bounds__(256) spread_es_atomic_kernel(SpreadArgs a)
 {
     __shared__ float tre[kTileY * kTileX];
     __shared__ float tim[kTileY * kTileX];
@@ -88,26 +208,15 @@ __global__ void __launch_bounds__(256) spread_es_kernel(SpreadArgs a)
         const float q = __ldg(&a.q[n]);
         const AxisEntry ex = a.ax[nx], ey = a.ay[ny];
         const AxisPos px = a.px[nx], py = a.py[ny];
-
-        // storage coordinate relative to bi: bf + s q; first tap l0 = bi + ceil(f)
-        const float fx = px.bf + ex.s * q - a.half_w;
-        const float fy = py.bf + ey.s * q - a.half_w;
-        const float cfx = ceilf(fx), cfy = ceilf(fy);
-        const int cx0 = (px.bi + (int)cfx - ox) & mx;  // tile-relative, wrapped to [0, nf)
-        const int cy0 = (py.bi + (int)cfy - oy) & my;
+        int l0x, l0y;
+        float dx, dy;
+        sample_pos(ex, ey, px, py, q, a.half_w, l0x, l0y, dx, dy);
+        const int cx0 = (l0x - ox) & mx;  // tile-relative, wrapped to [0, nf)
+        const int cy0 = (l0y - oy) & my;
         const bool hitx = (cx0 < kTileX) || (cx0 + W - 1 > mx);
         const bool hity = (cy0 < kTileY) || (cy0 + W - 1 > my);
         if (!(hitx && hity)) continue;
-        const float dx = cfx - fx, dy = cfy - fy;  // in [0, 1)
-
-        // prefactor c = u1 E_x E_y exp(i pi (a_x + a_y) q)
-        float sn, cs;
-        sincospif((ex.a + ey.a) * q, &sn, &cs);
-        const float2 u = __ldg(&a.u1[n]);
-        const float2 exy = make_float2(ex.e.x * ey.e.x - ex.e.y * ey.e.y,
-                                       ex.e.x * ey.e.y + ex.e.y * ey.e.x);
-        const float2 t1 = make_float2(u.x * exy.x - u.y * exy.y, u.x * exy.y + u.y * exy.x);
-        const float2 c = make_float2(t1.x * cs - t1.y * sn, t1.x * sn + t1.y * cs);
+        const float2 c = sample_value(__ldg(&a.u1[n]), ex, ey, q);
 
         float wx[W];
 #pragma unroll
@@ -145,9 +254,12 @@ __global__ void __launch_bounds__(256) spread_es_kernel(SpreadArgs a)
 }
 
 template <int W>
-cudaError_t launch_w(const SpreadArgs& a, int tiles, cudaStream_t st)
+cudaError_t launch_w(const SpreadArgs& a, int tiles, bool colored, cudaStream_t st)
 {
-    spread_es_kernel<W><<<tiles, 256, 0, st>>>(a);
+    if (colored)
+        spread_es_colored_kernel<W, kTileX, kColTileY><<<tiles * (kTileY / kColTileY), 32, 0, st>>>(a);
+    else
+        spread_es_atomic_kernel<W><<<tiles, 256, 0, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -164,6 +276,7 @@ asfd_status launch_spread(asfd_plan_s* P, const float2* u1, cudaStream_t st)
     a.py = P->py;
     a.tile_off = P->tile_off;
     a.tile_src = P->tile_src;
+    a.tile_rect = P->tile_rect;
     a.grid = P->grid;
     a.n1x = P->prm.n1x;
     a.n1y = P->prm.n1y;
@@ -173,31 +286,34 @@ asfd_status launch_spread(asfd_plan_s* P, const float2* u1, cudaStream_t st)
     a.band_tx0 = P->band_tx0;
     a.band_ty0 = P->band_ty0;
     a.band_ntx = P->band_tx1 - P->band_tx0;
+    a.sx_min = P->sx_min;
+    a.h_min = P->h_min;
     a.half_w = 0.5f * (float)P->w;
     a.beta_log2e = (float)(P->beta * 1.4426950408889634074);
     a.two_over_w = (float)(2.0 / P->w);
     const int tiles = (P->band_tx1 - P->band_tx0) * (P->band_ty1 - P->band_ty0);
     if (tiles <= 0) return ASFD_OK;
+    const bool colored = P->colored;
     cudaError_t e;
     switch (P->w) {
-        case 2: e = launch_w<2>(a, tiles, st); break;
-        case 3: e = launch_w<3>(a, tiles, st); break;
-        case 4: e = launch_w<4>(a, tiles, st); break;
-        case 5: e = launch_w<5>(a, tiles, st); break;
-        case 6: e = launch_w<6>(a, tiles, st); break;
-        case 7: e = launch_w<7>(a, tiles, st); break;
-        case 8: e = launch_w<8>(a, tiles, st); break;
-        case 9: e = launch_w<9>(a, tiles, st); break;
-        case 10: e = launch_w<10>(a, tiles, st); break;
-        case 11: e = launch_w<11>(a, tiles, st); break;
-        case 12: e = launch_w<12>(a, tiles, st); break;
-        case 13: e = launch_w<13>(a, tiles, st); break;
-        case 14: e = launch_w<14>(a, tiles, st); break;
-        case 15: e = launch_w<15>(a, tiles, st); break;
-        case 16: e = launch_w<16>(a, tiles, st); break;
+        case 2: e = launch_w<2>(a, tiles, colored, st); break;
+        case 3: e = launch_w<3>(a, tiles, colored, st); break;
+        case 4: e = launch_w<4>(a, tiles, colored, st); break;
+        case 5: e = launch_w<5>(a, tiles, colored, st); break;
+        case 6: e = launch_w<6>(a, tiles, colored, st); break;
+        case 7: e = launch_w<7>(a, tiles, colored, st); break;
+        case 8: e = launch_w<8>(a, tiles, colored, st); break;
+        case 9: e = launch_w<9>(a, tiles, colored, st); break;
+        case 10: e = launch_w<10>(a, tiles, colored, st); break;
+        case 11: e = launch_w<11>(a, tiles, colored, st); break;
+        case 12: e = launch_w<12>(a, tiles, colored, st); break;
+        case 13: e = launch_w<13>(a, tiles, colored, st); break;
+        case 14: e = launch_w<14>(a, tiles, colored, st); break;
+        case 15: e = launch_w<15>(a, tiles, colored, st); break;
+        case 16: e = launch_w<16>(a, tiles, colored, st); break;
         default: return fail(ASFD_ERR_UNSUPPORTED, "kernel width outside 2..16");
     }
-    if (e != cudaSuccess) return cuda_fail(e, "spread_es_kernel launch");
+    if (e != cudaSuccess) return cuda_fail(e, "spread kernel launch");
     return ASFD_OK;
 }
 

@@ -101,8 +101,33 @@ def test_periodic_wrap_full_grid():
     d1 = W.surface_sinusoid(g, 40e-6, 400e-6)
     out, info = run_gpu(g, u1, d1)
     assert info["band_x0"] == 0 and info["band_x1"] == info["nfx"]
+    assert info["spread_kind"] == 1  # wrapping footprints take the atomic kernel
     err = rel_l2(out, oracle.eq7(g, u1, d1))
     assert err < TOL_ES, err
+
+
+def test_folding_surface_uses_atomic_spread():
+    """A rough surface whose samples swap order on the fine grid (the map
+    n -> g is not monotone): the conflict-free kernel does not apply and the
+    shared-memory-atomic kernel must give the same accuracy."""
+    rng = np.random.default_rng(24)
+    g = W.geometry(64, 64, 10e-6, 10e-6, 64, 64, 10e-6, 10e-6, 633e-9, 0.05)
+    u1 = (rng.standard_normal((64, 64)) + 1j * rng.standard_normal((64, 64))).astype(np.complex64)
+    d1 = rng.uniform(-4e-3, 4e-3, (64, 64))
+    out, info = run_gpu(g, u1, d1)
+    assert info["spread_kind"] == 1
+    err = rel_l2(out, oracle.eq7(g, u1, d1))
+    assert err < TOL_ES, err
+
+
+@pytest.mark.parametrize("name", ["sinusoid64", "spherical_cap1024", "smooth_random2048",
+                                  "tilt_bump4096"])
+def test_standard_workloads_take_conflict_free_spread(name):
+    g, _, d1 = W.make(name)
+    with FresnelPlan(g, d1) as plan:
+        info = plan.info()
+    assert info["spread_kind"] == 0, info
+    assert info["stride_x"] >= 7 and info["stride_y"] >= 7
 
 
 def test_zero_field_gives_zero():
