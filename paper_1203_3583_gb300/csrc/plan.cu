@@ -479,6 +479,9 @@ asfd_status plan_build_d1(asfd_plan_s* P, const double* d1, cudaStream_t st)
         r.x1 = (int)std::floor((b[1] + hw) / kTileX);
         r.y0 = (int)std::floor((b[2] - hw) / kTileY);
         r.y1 = (int)std::floor((b[3] + hw) / kTileY);
+        // a footprint reaching outside [0, nf) wraps around the periodic grid
+        if (b[0] - hw < 0.0 || b[1] + hw > (double)P->nfx) wrapx = true;
+        if (b[2] - hw < 0.0 || b[3] + hw > (double)P->nfy) wrapy = true;
         if (r.x1 - r.x0 + 1 >= P->ntx) { r.x0 = 0; r.x1 = P->ntx - 1; }
         if (r.y1 - r.y0 + 1 >= P->nty) { r.y0 = 0; r.y1 = P->nty - 1; }
         if (r.x0 < 0 || r.x1 >= P->ntx) wrapx = true;
