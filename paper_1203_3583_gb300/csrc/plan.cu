@@ -578,7 +578,9 @@ asfd_status plan_build_colored(asfd_plan_s* P, bool wraps, cudaStream_t st)
     P->min_step_y = msy;
     P->row_spread_y = spread_y;
     const double margin = 0.01;
-    if (wraps || !(msx > 0.0) || !(msy > 0.0)) return ASFD_OK;
+    // the minimum spacing must clear FP32 rounding of the coordinates (~1e-6
+    // cells) so that the first tap column is non-decreasing along a row
+    if (wraps || !(msx > 1e-3) || !(msy > 1e-3) || P->w > kMaxRingWidth) return ASFD_OK;
     const double sxd = std::ceil((P->w + margin) / msx);
     const double hd = std::ceil((P->w + spread_y + margin) / msy);
     if (!(sxd <= 256.0) || !(hd <= 256.0)) return ASFD_OK;

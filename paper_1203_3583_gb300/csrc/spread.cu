@@ -108,6 +108,88 @@ __device__ __forceinline__ float2 fma2(float2 v, float w, float2 acc)
     return *reinterpret_cast<float2*>(&r);
 }
 
+// Per-sample inputs, loaded one sample ahead of use.
+struct Raw {
+    float q;
+    float2 u;
+    AxisEntry ex, ey;
+    AxisPos px, py;
+};
+
+__device__ __forceinline__ Raw load_raw(const SpreadArgs& a, int nx, int ny)
+{
+    Raw r;
+    const size_t n = (size_t)ny * a.n1x + nx;
+    r.q = __ldg(&a.q[n]);
+    r.u = __ldg(&a.u1[n]);
+    r.ex = a.ax[nx];
+    r.ey = a.ay[ny];
+    r.px = a.px[nx];
+    r.py = a.py[ny];
+    return r;
+}
+
+// ES weight with the approximate MUFU square root and exponential (relative
+// error ~2^-22, far below the kernel's own truncation error).
+__device__ __forceinline__ float es_weight_fast(float z, float two_over_w, float beta_log2e)
+{
+    const float u = z * two_over_w;
+    const float r = fmaxf(fmaf(-u, u, 1.0f), 1e-30f);
+    float rs, e;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(rs) : "f"(r));
+    const float arg = beta_log2e * fmaf(r, rs, -1.0f);
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(arg));
+    return e;
+}
+
+// c = u1 E_x E_y exp(i pi (a_x + a_y) q); the correction phase is reduced
+// modulo 2 half-turns exactly in FP32, then evaluated with the MUFU sine and
+// cosine (absolute error ~4e-7 on [-pi, pi]).
+__device__ __forceinline__ float2 sample_value_fast(const Raw& r)
+{
+    const float ph = (r.ex.a + r.ey.a) * r.q;
+    const float red = ph - 2.0f * rintf(0.5f * ph);
+    float sn, cs;
+    __sincosf(3.14159265358979f * red, &sn, &cs);
+    const float2 exy = make_float2(r.ex.e.x * r.ey.e.x - r.ex.e.y * r.ey.e.y,
+                                   r.ex.e.x * r.ey.e.y + r.ex.e.y * r.ey.e.x);
+    const float2 t1 = make_float2(r.u.x * exy.x - r.u.y * exy.y, r.u.x * exy.y + r.u.y * exy.x);
+    return make_float2(t1.x * cs - t1.y * sn, t1.x * sn + t1.y * cs);
+}
+
+// Adds the window slot `s` (column X, rows Y..Y+W-1) into the shared tile and clears it.
+template <int W, int TX, int TY, int LD>
+__device__ __forceinline__ void ring_flush(float2 (&acc)[W][W], int s, float2* tile, int X, int Y)
+{
+    if (X >= 0 && X < TX) {
+#pragma unroll
+        for (int b = 0; b < W; ++b) {
+            const int row = Y + b;
+            if (row >= 0 && row < TY) {
+                float2 v = tile[row * LD + X];
+                v.x += acc[b][s].x;
+                v.y += acc[b][s].y;
+                tile[row * LD + X] = v;
+            }
+        }
+    }
+#pragma unroll
+    for (int b = 0; b < W; ++b) acc[b][s] = make_float2(0.f, 0.f);
+}
+
+// Conflict-free spreading by a cell-driven sweep.  Each lane owns a run of
+// `sx` consecutive samples of one source row and walks the fine-grid columns
+// X of the run one step at a time, holding a W x W register window whose
+// ring slot (X - X0) mod W is the current column.  At each step it adds the
+// samples whose first tap column is X (the window then covers all their
+// taps), then adds the finished column X into shared memory.  Because X
+// advances by exactly one per step, the ring slot of every column is a
+// compile-time constant inside the W-fold unrolled step loop: no dynamic
+// register indexing, no register moves, and ~7 shared-memory updates per
+// sample instead of W^2.  The plan's strides keep the windows of the lanes of
+// one step disjoint (at least W + 1 columns or W rows apart), and a __syncwarp
+// per W steps orders the updates of neighbouring lanes, which reach a column
+// more than W steps apart.
 template <int W, int TX, int TY>
 __global__ void __launch_bounds__(32) spread_es_colored_kernel(SpreadArgs a)
 {
@@ -130,37 +212,75 @@ __global__ void __launch_bounds__(32) spread_es_colored_kernel(SpreadArgs a)
         const int h = max(a.h_min, (rh + 3) / 4);
         for (int j = 0; j < h; ++j) {
             const int ny = rc.z + lr * h + j;
-            for (int o = 0; o < sx; ++o) {
-                const int nx = rc.x + lc * sx + o;
-                if (nx < rc.y && ny < rc.w) {
-                    const size_t n = (size_t)ny * a.n1x + nx;
-                    const float q = __ldg(&a.q[n]);
-                    const AxisEntry ex = a.ax[nx], ey = a.ay[ny];
-                    const AxisPos px = a.px[nx], py = a.py[ny];
-                    int l0x, l0y;
-                    float dx, dy;
-                    sample_pos(ex, ey, px, py, q, a.half_w, l0x, l0y, dx, dy);
-                    const int cx = l0x - ox, cy = l0y - oy;
-                    if (cx > -W && cx < TX && cy > -W && cy < TY) {
-                        const float2 c = sample_value(__ldg(&a.u1[n]), ex, ey, q);
-                        float wx[W];
+            const int nx_end = min(rc.x + lc * sx + sx, rc.y);
+            int nx = rc.x + lc * sx;
+            bool live = (ny < rc.w) && (nx < nx_end);
+            float2 acc[W][W];
 #pragma unroll
-                        for (int i = 0; i < W; ++i)
-                            wx[i] = es_weight(dx + (float)i - a.half_w, a.two_over_w, a.beta_log2e);
+            for (int b = 0; b < W; ++b)
 #pragma unroll
-                        for (int b = 0; b < W; ++b) {
-                            const int row = cy + b;
-                            if (row < 0 || row >= TY) continue;
-                            const float wy = es_weight(dy + (float)b - a.half_w, a.two_over_w,
-                                                       a.beta_log2e);
-                            const float2 cb = make_float2(c.x * wy, c.y * wy);
-                            float2* tr = tile + row * LD;
+                for (int s = 0; s < W; ++s) acc[b][s] = make_float2(0.f, 0.f);
+            int X = 0, Y = 0, cx = 0, cy = 0;
+            float dx = 0.f, dy = 0.f;
+            Raw cur, pre;
+            if (live) {
+                cur = load_raw(a, nx, ny);
+                int l0x, l0y;
+                sample_pos(cur.ex, cur.ey, cur.px, cur.py, cur.q, a.half_w, l0x, l0y, dx, dy);
+                cx = l0x - ox;
+                cy = l0y - oy;
+                X = cx;
+                Y = cy;
+                if (nx + 1 < nx_end) pre = load_raw(a, nx + 1, ny);
+            }
+            while (__any_sync(0xffffffffu, live)) {
 #pragma unroll
-                            for (int i = 0; i < W; ++i) {
-                                const int col = cx + i;
-                                if (col < 0 || col >= TX) continue;
-                                tr[col] = fma2(cb, wx[i], tr[col]);
+                for (int r = 0; r < W; ++r) {
+                    if (live) {
+                        while (nx < nx_end && cx == X) {
+                            if (cy != Y) {  // rare: the row's y anchor moves by a cell
+#pragma unroll
+                                for (int i = 0; i < W; ++i)
+                                    ring_flush<W, TX, TY, LD>(acc, (r + i) % W, tile, X + i, Y);
+                                Y = cy;
                             }
+                            if (cx > -W && cx < TX && cy > -W && cy < TY) {
+                                const float2 c = sample_value_fast(cur);
+                                float wx[W];
+#pragma unroll
+                                for (int i = 0; i < W; ++i)
+                                    wx[i] = es_weight_fast(dx + (float)i - a.half_w, a.two_over_w,
+                                                           a.beta_log2e);
+#pragma unroll
+                                for (int b = 0; b < W; ++b) {
+                                    const float wy = es_weight_fast(dy + (float)b - a.half_w,
+                                                                    a.two_over_w, a.beta_log2e);
+                                    const float2 cb = make_float2(c.x * wy, c.y * wy);
+#pragma unroll
+                                    for (int i = 0; i < W; ++i)
+                                        acc[b][(r + i) % W] = fma2(cb, wx[i], acc[b][(r + i) % W]);
+                                }
+                            }
+                            ++nx;
+                            if (nx < nx_end) {
+                                cur = pre;
+                                int l0x, l0y;
+                                sample_pos(cur.ex, cur.ey, cur.px, cur.py, cur.q, a.half_w, l0x,
+                                           l0y, dx, dy);
+                                cx = l0x - ox;
+                                cy = l0y - oy;
+                                if (nx + 1 < nx_end) pre = load_raw(a, nx + 1, ny);
+                            }
+                        }
+                        if (nx < nx_end) {
+                            ring_flush<W, TX, TY, LD>(acc, r, tile, X, Y);
+                            ++X;
+                        } else {
+                            // run finished: the window holds columns X .. X+W-1
+#pragma unroll
+                            for (int i = 0; i < W; ++i)
+                                ring_flush<W, TX, TY, LD>(acc, (r + i) % W, tile, X + i, Y);
+                            live = false;
                         }
                     }
                 }
@@ -256,10 +376,15 @@ __global__ void __launch_bounds__(256) spread_es_atomic_kernel(SpreadArgs a)
 template <int W>
 cudaError_t launch_w(const SpreadArgs& a, int tiles, bool colored, cudaStream_t st)
 {
-    if (colored)
-        spread_es_colored_kernel<W, kTileX, kColTileY><<<tiles * (kTileY / kColTileY), 32, 0, st>>>(a);
-    else
-        spread_es_atomic_kernel<W><<<tiles, 256, 0, st>>>(a);
+    // the W x W register window fits the register file up to W = kMaxRingWidth
+    if constexpr (W <= kMaxRingWidth) {
+        if (colored) {
+            spread_es_colored_kernel<W, kTileX, kColTileY>
+                <<<tiles * (kTileY / kColTileY), 32, 0, st>>>(a);
+            return cudaGetLastError();
+        }
+    }
+    spread_es_atomic_kernel<W><<<tiles, 256, 0, st>>>(a);
     return cudaGetLastError();
 }
 
