@@ -18,7 +18,7 @@ constexpr int kTileX = 64;
 constexpr int kTileY = 64;
 constexpr int kSrcTile = 16;  // source tiles are kSrcTile x kSrcTile samples
 constexpr int kColTileY = 32; // rows of a tile of the conflict-free spreading kernel
-constexpr int kMaxRingWidth = 8;  // widest kernel whose W x W window fits in registers
+constexpr int kMaxRingWidth = 14;  // widest kernel of the conflict-free spreading path (no spills)
 
 // Device status word bits (set by kernels, read by asfd_check_device_status).
 constexpr unsigned kStatusBadD1 = 1u;       // non-finite d1 or d1 >= z0

@@ -157,39 +157,14 @@ __device__ __forceinline__ float2 sample_value_fast(const Raw& r)
     return make_float2(t1.x * cs - t1.y * sn, t1.x * sn + t1.y * cs);
 }
 
-// Adds the window slot `s` (column X, rows Y..Y+W-1) into the shared tile and clears it.
-template <int W, int TX, int TY, int LD>
-__device__ __forceinline__ void ring_flush(float2 (&acc)[W][W], int s, float2* tile, int X, int Y)
-{
-    if (X >= 0 && X < TX) {
-#pragma unroll
-        for (int b = 0; b < W; ++b) {
-            const int row = Y + b;
-            if (row >= 0 && row < TY) {
-                float2 v = tile[row * LD + X];
-                v.x += acc[b][s].x;
-                v.y += acc[b][s].y;
-                tile[row * LD + X] = v;
-            }
-        }
-    }
-#pragma unroll
-    for (int b = 0; b < W; ++b) acc[b][s] = make_float2(0.f, 0.f);
-}
-
-// Conflict-free spreading by a cell-driven sweep.  Each lane owns a run of
-// `sx` consecutive samples of one source row and walks the fine-grid columns
-// X of the run one step at a time, holding a W x W register window whose
-// ring slot (X - X0) mod W is the current column.  At each step it adds the
-// samples whose first tap column is X (the window then covers all their
-// taps), then adds the finished column X into shared memory.  Because X
-// advances by exactly one per step, the ring slot of every column is a
-// compile-time constant inside the W-fold unrolled step loop: no dynamic
-// register indexing, no register moves, and ~7 shared-memory updates per
-// sample instead of W^2.  The plan's strides keep the windows of the lanes of
-// one step disjoint (at least W + 1 columns or W rows apart), and a __syncwarp
-// per W steps orders the updates of neighbouring lanes, which reach a column
-// more than W steps apart.
+// Conflict-free spreading: one warp per tile, plain shared-memory
+// read-modify-write.  Lanes form 4 row groups x 8 column groups; at step
+// (j, o) lane (lr, lc) takes sample (x0 + lc sx + o, y0 + lr h + j).  The
+// plan's strides make the footprints of the 32 samples of one step pairwise
+// disjoint (same row: sx columns apart, different rows: h rows apart), so the
+// 49 taps of a lane are loaded, updated and stored as independent operations,
+// and a __syncwarp orders consecutive steps.  The inputs of the next step are
+// loaded while the current one is processed.
 template <int W, int TX, int TY>
 __global__ void __launch_bounds__(32) spread_es_colored_kernel(SpreadArgs a)
 {
@@ -210,82 +185,67 @@ __global__ void __launch_bounds__(32) spread_es_colored_kernel(SpreadArgs a)
         const int lc = lane & 7, lr = lane >> 3;
         const int sx = max(a.sx_min, (rw + 7) / 8);
         const int h = max(a.h_min, (rh + 3) / 4);
-        for (int j = 0; j < h; ++j) {
-            const int ny = rc.z + lr * h + j;
-            const int nx_end = min(rc.x + lc * sx + sx, rc.y);
-            int nx = rc.x + lc * sx;
-            bool live = (ny < rc.w) && (nx < nx_end);
-            float2 acc[W][W];
-#pragma unroll
-            for (int b = 0; b < W; ++b)
-#pragma unroll
-                for (int s = 0; s < W; ++s) acc[b][s] = make_float2(0.f, 0.f);
-            int X = 0, Y = 0, cx = 0, cy = 0;
-            float dx = 0.f, dy = 0.f;
-            Raw cur, pre;
-            if (live) {
-                cur = load_raw(a, nx, ny);
-                int l0x, l0y;
-                sample_pos(cur.ex, cur.ey, cur.px, cur.py, cur.q, a.half_w, l0x, l0y, dx, dy);
-                cx = l0x - ox;
-                cy = l0y - oy;
-                X = cx;
-                Y = cy;
-                if (nx + 1 < nx_end) pre = load_raw(a, nx + 1, ny);
+        const int nx0 = rc.x + lc * sx, ny0 = rc.z + lr * h;
+        const int steps = h * sx;
+        int j = 0, o = 0;
+        bool v = (nx0 < rc.y) && (ny0 < rc.w);
+        Raw cur;
+        if (v) cur = load_raw(a, nx0, ny0);
+        for (int k = 0; k < steps; ++k) {
+            // inputs of step k + 1
+            int j2 = j, o2 = o + 1;
+            if (o2 == sx) {
+                o2 = 0;
+                ++j2;
             }
-            while (__any_sync(0xffffffffu, live)) {
+            const bool v2 = (k + 1 < steps) && (nx0 + o2 < rc.y) && (ny0 + j2 < rc.w);
+            Raw nxt;
+            if (v2) nxt = load_raw(a, nx0 + o2, ny0 + j2);
+            if (v) {
+                int l0x, l0y;
+                float dx, dy;
+                sample_pos(cur.ex, cur.ey, cur.px, cur.py, cur.q, a.half_w, l0x, l0y, dx, dy);
+                const int cx = l0x - ox, cy = l0y - oy;
+                if (cx > -W && cx < TX && cy > -W && cy < TY) {
+                    const float2 c = sample_value_fast(cur);
+                    float wx[W], wy[W];
+                    bool colok[W];
 #pragma unroll
-                for (int r = 0; r < W; ++r) {
-                    if (live) {
-                        while (nx < nx_end && cx == X) {
-                            if (cy != Y) {  // rare: the row's y anchor moves by a cell
+                    for (int i = 0; i < W; ++i) {
+                        wx[i] = es_weight_fast(dx + (float)i - a.half_w, a.two_over_w, a.beta_log2e);
+                        wy[i] = es_weight_fast(dy + (float)i - a.half_w, a.two_over_w, a.beta_log2e);
+                        colok[i] = (unsigned)(cx + i) < (unsigned)TX;
+                    }
+                    // taps of this lane are distinct cells: load all, update, store all
+                    float2* base = tile + cy * LD + cx;
+                    float2 acc[W][W];
 #pragma unroll
-                                for (int i = 0; i < W; ++i)
-                                    ring_flush<W, TX, TY, LD>(acc, (r + i) % W, tile, X + i, Y);
-                                Y = cy;
-                            }
-                            if (cx > -W && cx < TX && cy > -W && cy < TY) {
-                                const float2 c = sample_value_fast(cur);
-                                float wx[W];
+                    for (int b = 0; b < W; ++b) {
+                        const bool rowok = (unsigned)(cy + b) < (unsigned)TY;
 #pragma unroll
-                                for (int i = 0; i < W; ++i)
-                                    wx[i] = es_weight_fast(dx + (float)i - a.half_w, a.two_over_w,
-                                                           a.beta_log2e);
+                        for (int i = 0; i < W; ++i)
+                            acc[b][i] = (rowok && colok[i]) ? base[b * LD + i] : make_float2(0.f, 0.f);
+                    }
 #pragma unroll
-                                for (int b = 0; b < W; ++b) {
-                                    const float wy = es_weight_fast(dy + (float)b - a.half_w,
-                                                                    a.two_over_w, a.beta_log2e);
-                                    const float2 cb = make_float2(c.x * wy, c.y * wy);
+                    for (int b = 0; b < W; ++b) {
+                        const float2 cb = make_float2(c.x * wy[b], c.y * wy[b]);
 #pragma unroll
-                                    for (int i = 0; i < W; ++i)
-                                        acc[b][(r + i) % W] = fma2(cb, wx[i], acc[b][(r + i) % W]);
-                                }
-                            }
-                            ++nx;
-                            if (nx < nx_end) {
-                                cur = pre;
-                                int l0x, l0y;
-                                sample_pos(cur.ex, cur.ey, cur.px, cur.py, cur.q, a.half_w, l0x,
-                                           l0y, dx, dy);
-                                cx = l0x - ox;
-                                cy = l0y - oy;
-                                if (nx + 1 < nx_end) pre = load_raw(a, nx + 1, ny);
-                            }
-                        }
-                        if (nx < nx_end) {
-                            ring_flush<W, TX, TY, LD>(acc, r, tile, X, Y);
-                            ++X;
-                        } else {
-                            // run finished: the window holds columns X .. X+W-1
+                        for (int i = 0; i < W; ++i) acc[b][i] = fma2(cb, wx[i], acc[b][i]);
+                    }
 #pragma unroll
-                            for (int i = 0; i < W; ++i)
-                                ring_flush<W, TX, TY, LD>(acc, (r + i) % W, tile, X + i, Y);
-                            live = false;
-                        }
+                    for (int b = 0; b < W; ++b) {
+                        const bool rowok = (unsigned)(cy + b) < (unsigned)TY;
+#pragma unroll
+                        for (int i = 0; i < W; ++i)
+                            if (rowok && colok[i]) base[b * LD + i] = acc[b][i];
                     }
                 }
-                __syncwarp();
             }
+            __syncwarp();
+            cur = nxt;
+            v = v2;
+            j = j2;
+            o = o2;
         }
     }
     __syncwarp();
