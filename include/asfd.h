@@ -142,6 +142,27 @@ asfd_status asfd_execute_host(asfd_plan plan, const float* u1_host, float* u2_ho
 asfd_status asfd_execute_stage(asfd_plan plan, int stage, const float* u1_dev, float* u2_dev,
                                void* stream);
 
+/*
+ * Adjoint (type-2 NUFFT) of asfd_execute, for gradients of a real loss L(u2)
+ * with respect to the source field and the height map (hologram and surface
+ * optimisation).  grad_u2_dev: device [m2y][m2x] complex holding
+ * dL/dRe(u2) + i dL/dIm(u2).  Writes, for every source sample n,
+ *   grad_u1_dev[n] = dL/dRe(u1) + i dL/dIm(u1) = sum_m conj(K_mn) grad_u2[m]
+ *   grad_d1_dev[n] = dL/dd1[n]   (FP32, per metre)
+ * where K_mn is the coefficient of u1[n] in u2[m] as the forward computes it
+ * (Eq. 8 with the plan's kernel): the conjugate transpose of the forward
+ * map, and the derivative of that map through the phase k|x1|^2/(2 r0) and
+ * the non-uniform frequency k p2 x1 / r0 of each sample.  Stages: column
+ * FFT with e^{+i} of conj(deconvolution x chirp) * grad_u2, row FFT with
+ * e^{+i}, then one interpolation kernel with the kernel and its derivative.
+ * grad_u1_dev and grad_d1_dev may each be NULL (not computed); u1_dev may be
+ * NULL only when grad_d1_dev is NULL.  Uses the plan's work buffers (not
+ * concurrent with asfd_execute on the same plan).  Asynchronous.
+ * Errors: ASFD_ERR_ARG (NULL grad_u2, or grad_d1 without u1), ASFD_ERR_CUDA.
+ */
+asfd_status asfd_adjoint(asfd_plan plan, const float* u1_dev, const float* grad_u2_dev,
+                         float* grad_u1_dev, float* grad_d1_dev, void* stream);
+
 /* Fill *info.  Errors: ASFD_ERR_ARG. */
 asfd_status asfd_get_plan_info(asfd_plan plan, asfd_plan_info* info);
 

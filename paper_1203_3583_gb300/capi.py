@@ -75,6 +75,7 @@ SIGNATURES = {
     "asfd_execute": (_int, [_vp, _vp, _vp, _vp]),
     "asfd_execute_host": (_int, [_vp, _vp, _vp, _vp]),
     "asfd_execute_stage": (_int, [_vp, _int, _vp, _vp, _vp]),
+    "asfd_adjoint": (_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
     "asfd_get_plan_info": (_int, [_vp, ctypes.POINTER(PlanInfo)]),
     "asfd_check_device_status": (_int, [_vp, _vp]),
     "asfd_destroy": (_int, [_vp]),
@@ -166,6 +167,15 @@ def asfd_execute_stage(plan, stage: int, u1, u2, shape1, shape2, stream=None) ->
     p1 = _dev_ptr(u1, torch.complex64, shape1, "u1") if u1 is not None else None
     p2 = _dev_ptr(u2, torch.complex64, shape2, "u2") if u2 is not None else None
     _check(lib.asfd_execute_stage(plan, int(stage), p1, p2, _stream(stream)))
+
+
+def asfd_adjoint(plan, u1, grad_u2, grad_u1, grad_d1, shape1, shape2, stream=None) -> None:
+    lib = load()
+    p_u1 = _dev_ptr(u1, torch.complex64, shape1, "u1") if u1 is not None else None
+    p_g2 = _dev_ptr(grad_u2, torch.complex64, shape2, "grad_u2")
+    p_g1 = _dev_ptr(grad_u1, torch.complex64, shape1, "grad_u1") if grad_u1 is not None else None
+    p_gd = _dev_ptr(grad_d1, torch.float32, shape1, "grad_d1") if grad_d1 is not None else None
+    _check(lib.asfd_adjoint(plan, p_u1, p_g2, p_g1, p_gd, _stream(stream)))
 
 
 def asfd_execute_host(plan, u1: torch.Tensor, u2: torch.Tensor, shape1, shape2, stream=None) -> None:

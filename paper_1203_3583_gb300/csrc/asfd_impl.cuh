@@ -123,6 +123,10 @@ asfd_status launch_fft_rows(asfd_plan_s* P, cudaStream_t st);
 asfd_status launch_fft_cols(asfd_plan_s* P, float2* u2, cudaStream_t st);
 asfd_status launch_fft_lines(int n, int lines, int sign, const float2* in, float2* out,
                              cudaStream_t st);
+asfd_status launch_fft_cols_adj(asfd_plan_s* P, const float2* g, cudaStream_t st);
+asfd_status launch_fft_rows_adj(asfd_plan_s* P, cudaStream_t st);
+asfd_status launch_interp_grad(asfd_plan_s* P, const float2* u1, float2* gu1, float* gd1,
+                               cudaStream_t st);
 
 // plan helpers
 asfd_status plan_validate(const asfd_params* p, int* nfx, int* nfy, double* beta);

@@ -146,6 +146,24 @@ asfd_status asfd_execute_stage(asfd_plan P, int stage, const float* u1_dev, floa
     });
 }
 
+asfd_status asfd_adjoint(asfd_plan P, const float* u1_dev, const float* grad_u2_dev,
+                         float* grad_u1_dev, float* grad_d1_dev, void* stream)
+{
+    clear_error();
+    if (!P || !grad_u2_dev) return fail(ASFD_ERR_ARG, "plan or grad_u2 is NULL");
+    if (grad_d1_dev && !u1_dev) return fail(ASFD_ERR_ARG, "grad_d1 needs u1");
+    if (!grad_u1_dev && !grad_d1_dev) return ASFD_OK;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    return on_device(P->device, [&]() -> asfd_status {
+        asfd_status s = launch_fft_cols_adj(P, reinterpret_cast<const float2*>(grad_u2_dev), st);
+        if (s != ASFD_OK) return s;
+        s = launch_fft_rows_adj(P, st);
+        if (s != ASFD_OK) return s;
+        return launch_interp_grad(P, reinterpret_cast<const float2*>(u1_dev),
+                                  reinterpret_cast<float2*>(grad_u1_dev), grad_d1_dev, st);
+    });
+}
+
 asfd_status asfd_execute_host(asfd_plan P, const float* u1_host, float* u2_host, void* stream)
 {
     clear_error();

@@ -92,6 +92,65 @@ fft_cols_kernel(const float2* __restrict__ rows, int row0, int nrows, int m2x, i
     fft_line<L, -1>(t, sm + c * C::LS, tw, ld, st);
 }
 
+// Adjoint column pass: h = conj(Cx Cy) gu2 placed at the kept bins, FFT with
+// e^{+i} along y, band rows [row0, row0 + nrows) stored to rows[s - row0][kx].
+template <int L>
+__global__ void __launch_bounds__(ColCfg<L>::THREADS)
+fft_cols_adj_kernel(const float2* __restrict__ g, int m2x, int m2y, const float2* __restrict__ cx,
+                    const float2* __restrict__ cy, float2* __restrict__ rows, int row0, int nrows,
+                    const float2* __restrict__ tw)
+{
+    using C = ColCfg<L>;
+    extern __shared__ float2 sm[];
+    const int c = threadIdx.x % C::LPC, t = threadIdx.x / C::LPC;
+    const int col = blockIdx.x * C::LPC + c;
+    const bool active = col < m2x;
+    const int colc = active ? col : 0;
+    const float2 fx = __ldg(&cx[colc]);
+    const int half = m2y / 2;
+    auto ld = [&](int i) -> float2 {
+        int k;
+        if (i < half) k = i + half;
+        else if (i >= L - half) k = i - (L - half);
+        else return make_float2(0.f, 0.f);
+        if (!active) return make_float2(0.f, 0.f);
+        // conj(fx * cy[k]) * g
+        return cmulc(cmulc(__ldg(&g[(size_t)k * m2x + colc]), fx), __ldg(&cy[k]));
+    };
+    auto st = [&](int i, float2 v) {
+        const int rr = i - row0;
+        if (active && rr >= 0 && rr < nrows) rows[(size_t)rr * m2x + colc] = v;
+    };
+    fft_line<L, 1>(t, sm + c * C::LS, tw, ld, st);
+}
+
+// Adjoint row pass: band row r of rows[][] placed at the kept bins, FFT with
+// e^{+i} along x, band columns [col_lo, col_hi) stored to the fine grid.
+template <int L>
+__global__ void __launch_bounds__(RowCfg<L>::THREADS)
+fft_rows_adj_kernel(const float2* __restrict__ rows, int nrows, int m2x, float2* __restrict__ grid,
+                    int row0, int col_lo, int col_hi, const float2* __restrict__ tw)
+{
+    using C = RowCfg<L>;
+    extern __shared__ float2 sm[];
+    const int line = threadIdx.x / C::TPL, t = threadIdx.x % C::TPL;
+    const int r = blockIdx.x * C::LPC + line;
+    const bool active = r < nrows;
+    const float2* src = rows + (size_t)(active ? r : 0) * m2x;
+    float2* dst = grid + (size_t)(row0 + (active ? r : 0)) * L;
+    const int half = m2x / 2;
+    auto ld = [&](int i) -> float2 {
+        if (!active) return make_float2(0.f, 0.f);
+        if (i < half) return __ldg(&src[i + half]);
+        if (i >= L - half) return __ldg(&src[i - (L - half)]);
+        return make_float2(0.f, 0.f);
+    };
+    auto st = [&](int i, float2 v) {
+        if (active && i >= col_lo && i < col_hi) dst[i] = v;
+    };
+    fft_line<L, 1>(t, sm + line * C::LS, tw, ld, st);
+}
+
 template <int L, int S>
 __global__ void __launch_bounds__(RowCfg<L>::THREADS)
 fft_lines_kernel(const float2* in, float2* out, int lines, const float2* __restrict__ tw)
@@ -144,6 +203,36 @@ cudaError_t cols_L(const float2* rows, int row0, int nrows, int m2x, int m2y, co
     const int blocks = (m2x + C::LPC - 1) / C::LPC;
     fft_cols_kernel<L><<<blocks, C::THREADS, C::SMEM_BYTES, st>>>(rows, row0, nrows, m2x, m2y,
                                                                   cx, cy, u2, tw);
+    return cudaGetLastError();
+}
+
+template <int L>
+cudaError_t cols_adj_L(const float2* g, int m2x, int m2y, const float2* cx, const float2* cy,
+                       float2* rows, int row0, int nrows, const float2* tw, cudaStream_t st)
+{
+    using C = ColCfg<L>;
+    static std::once_flag once;
+    static cudaError_t attr = cudaSuccess;
+    std::call_once(once, [] { attr = set_smem(fft_cols_adj_kernel<L>, C::SMEM_BYTES); });
+    if (attr != cudaSuccess) return attr;
+    const int blocks = (m2x + C::LPC - 1) / C::LPC;
+    fft_cols_adj_kernel<L><<<blocks, C::THREADS, C::SMEM_BYTES, st>>>(g, m2x, m2y, cx, cy, rows,
+                                                                      row0, nrows, tw);
+    return cudaGetLastError();
+}
+
+template <int L>
+cudaError_t rows_adj_L(const float2* rows, int nrows, int m2x, float2* grid, int row0, int col_lo,
+                       int col_hi, const float2* tw, cudaStream_t st)
+{
+    using C = RowCfg<L>;
+    static std::once_flag once;
+    static cudaError_t attr = cudaSuccess;
+    std::call_once(once, [] { attr = set_smem(fft_rows_adj_kernel<L>, C::SMEM_BYTES); });
+    if (attr != cudaSuccess) return attr;
+    const int blocks = (nrows + C::LPC - 1) / C::LPC;
+    fft_rows_adj_kernel<L><<<blocks, C::THREADS, C::SMEM_BYTES, st>>>(rows, nrows, m2x, grid, row0,
+                                                                      col_lo, col_hi, tw);
     return cudaGetLastError();
 }
 
@@ -211,6 +300,32 @@ asfd_status launch_fft_cols(asfd_plan_s* P, float2* u2, cudaStream_t st)
     ASFD_FFT_SWITCH(P->nfy, ASFD_COLS)
 #undef ASFD_COLS
     if (e != cudaSuccess) return cuda_fail(e, "fft_cols_kernel launch");
+    return ASFD_OK;
+}
+
+asfd_status launch_fft_cols_adj(asfd_plan_s* P, const float2* g, cudaStream_t st)
+{
+    const int row0 = P->band_ty0 * kTileY;
+    const int nrows = (P->band_ty1 - P->band_ty0) * kTileY;
+    cudaError_t e = cudaSuccess;
+#define ASFD_CA(L) e = cols_adj_L<L>(g, P->prm.m2x, P->prm.m2y, P->cx, P->cy, P->rows, row0, nrows, P->twy, st)
+    ASFD_FFT_SWITCH(P->nfy, ASFD_CA)
+#undef ASFD_CA
+    if (e != cudaSuccess) return cuda_fail(e, "fft_cols_adj_kernel launch");
+    return ASFD_OK;
+}
+
+asfd_status launch_fft_rows_adj(asfd_plan_s* P, cudaStream_t st)
+{
+    const int row0 = P->band_ty0 * kTileY;
+    const int nrows = (P->band_ty1 - P->band_ty0) * kTileY;
+    const int col_lo = P->band_tx0 * kTileX, col_hi = P->band_tx1 * kTileX;
+    if (nrows <= 0) return ASFD_OK;
+    cudaError_t e = cudaSuccess;
+#define ASFD_RA(L) e = rows_adj_L<L>(P->rows, nrows, P->prm.m2x, P->grid, row0, col_lo, col_hi, P->twx, st)
+    ASFD_FFT_SWITCH(P->nfx, ASFD_RA)
+#undef ASFD_RA
+    if (e != cudaSuccess) return cuda_fail(e, "fft_rows_adj_kernel launch");
     return ASFD_OK;
 }
 

@@ -1,0 +1,130 @@
+// Per-sample arithmetic shared by the spreading (forward) and interpolation
+// (adjoint) kernels: the sample's position on the fine grid, its prefactor
+// and the exponential-of-semicircle kernel weights.  See spread.cu for the
+// phase and position split between the FP64 plan tables and the FP32
+// per-sample corrections.
+#pragma once
+
+#include "asfd_impl.cuh"
+
+namespace asfd {
+
+// ES kernel psi(z) = exp(beta (sqrt(1 - (2z/w)^2) - 1)), |z| <= w/2.
+__device__ __forceinline__ float es_weight(float z, float two_over_w, float beta_log2e)
+{
+    const float u = z * two_over_w;
+    const float r = fmaxf(1.0f - u * u, 0.0f);
+    const float s = r > 0.0f ? r * rsqrtf(r) : 0.0f;
+    return exp2f(beta_log2e * (s - 1.0f));
+}
+
+// First tap (storage coordinates, not wrapped) and fractional offset of a sample.
+__device__ __forceinline__ void sample_pos(const AxisEntry& ex, const AxisEntry& ey,
+                                           const AxisPos& px, const AxisPos& py, float q,
+                                           float half_w, int& l0x, int& l0y, float& dx, float& dy)
+{
+    const float fx = px.bf + ex.s * q - half_w;
+    const float fy = py.bf + ey.s * q - half_w;
+    const float cfx = ceilf(fx), cfy = ceilf(fy);
+    l0x = px.bi + (int)cfx;
+    l0y = py.bi + (int)cfy;
+    dx = cfx - fx;  // in [0, 1): tap i sits at dx + i - w/2 from the sample
+    dy = cfy - fy;
+}
+
+// c = u1 E_x E_y exp(i pi (a_x + a_y) q)
+__device__ __forceinline__ float2 sample_value(float2 u, const AxisEntry& ex, const AxisEntry& ey,
+                                               float q)
+{
+    float sn, cs;
+    sincospif((ex.a + ey.a) * q, &sn, &cs);
+    const float2 exy = make_float2(ex.e.x * ey.e.x - ex.e.y * ey.e.y,
+                                   ex.e.x * ey.e.y + ex.e.y * ey.e.x);
+    const float2 t1 = make_float2(u.x * exy.x - u.y * exy.y, u.x * exy.y + u.y * exy.x);
+    return make_float2(t1.x * cs - t1.y * sn, t1.x * sn + t1.y * cs);
+}
+
+// acc + v * w on a complex pair (packed FP32x2 FMA)
+__device__ __forceinline__ float2 fma2(float2 v, float w, float2 acc)
+{
+    unsigned long long r;
+    const unsigned long long vv = *reinterpret_cast<const unsigned long long*>(&v);
+    const unsigned long long aa = *reinterpret_cast<const unsigned long long*>(&acc);
+    const float2 ww = make_float2(w, w);
+    const unsigned long long wb = *reinterpret_cast<const unsigned long long*>(&ww);
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(vv), "l"(wb), "l"(aa));
+    return *reinterpret_cast<float2*>(&r);
+}
+
+// Per-sample inputs, loaded one sample ahead of use.
+struct Raw {
+    float q;
+    float2 u;
+    AxisEntry ex, ey;
+    AxisPos px, py;
+};
+
+template <class Args>
+__device__ __forceinline__ Raw load_raw(const Args& a, int nx, int ny)
+{
+    Raw r;
+    const size_t n = (size_t)ny * a.n1x + nx;
+    r.q = __ldg(&a.q[n]);
+    r.u = __ldg(&a.u1[n]);
+    r.ex = a.ax[nx];
+    r.ey = a.ay[ny];
+    r.px = a.px[nx];
+    r.py = a.py[ny];
+    return r;
+}
+
+// ES weight with the approximate MUFU square root and exponential (relative
+// error ~2^-22, far below the kernel's own truncation error).
+__device__ __forceinline__ float es_weight_fast(float z, float two_over_w, float beta_log2e)
+{
+    const float u = z * two_over_w;
+    const float r = fmaxf(fmaf(-u, u, 1.0f), 1e-30f);
+    float rs, e;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(rs) : "f"(r));
+    const float arg = beta_log2e * fmaf(r, rs, -1.0f);
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(arg));
+    return e;
+}
+
+// c = u1 E_x E_y exp(i pi (a_x + a_y) q); the correction phase is reduced
+// modulo 2 half-turns exactly in FP32, then evaluated with the MUFU sine and
+// cosine (absolute error ~4e-7 on [-pi, pi]).
+__device__ __forceinline__ float2 sample_value_fast(const Raw& r)
+{
+    const float ph = (r.ex.a + r.ey.a) * r.q;
+    const float red = ph - 2.0f * rintf(0.5f * ph);
+    float sn, cs;
+    __sincosf(3.14159265358979f * red, &sn, &cs);
+    const float2 exy = make_float2(r.ex.e.x * r.ey.e.x - r.ex.e.y * r.ey.e.y,
+                                   r.ex.e.x * r.ey.e.y + r.ex.e.y * r.ey.e.x);
+    const float2 t1 = make_float2(r.u.x * exy.x - r.u.y * exy.y, r.u.x * exy.y + r.u.y * exy.x);
+    return make_float2(t1.x * cs - t1.y * sn, t1.x * sn + t1.y * cs);
+}
+
+}  // namespace asfd
+
+namespace asfd {
+
+// psi(z) and d psi / dz of the ES kernel at z (fast MUFU forms).  The
+// derivative -psi beta (2/w) u / sqrt(1 - u^2) is infinite at the support
+// edge, where psi itself is e^-beta; 1 - u^2 is floored at 1e-12 so that the
+// edge tap (weight ~e^-beta) stays finite.
+__device__ __forceinline__ void es_weight_deriv_fast(float z, float two_over_w, float beta_log2e,
+                                                     float beta, float& psi, float& dpsi)
+{
+    const float u = z * two_over_w;
+    const float r = fmaxf(fmaf(-u, u, 1.0f), 1e-12f);
+    float rs, e;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(rs) : "f"(r));
+    const float arg = beta_log2e * fmaf(r, rs, -1.0f);
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(arg));
+    psi = e;
+    dpsi = -e * beta * two_over_w * u * rs;
+}
+
+}  // namespace asfd

@@ -55,6 +55,21 @@ class FresnelPlan:
     def execute_stage(self, stage: int, u1=None, out=None, stream=None) -> None:
         capi.asfd_execute_stage(self.handle, stage, u1, out, self.shape1, self.shape2, stream)
 
+    def adjoint(self, u1, grad_u2: torch.Tensor, grad_u1=None, grad_d1=None, stream=None):
+        """Type-2 adjoint: fills grad_u1 (complex64) and/or grad_d1 (float32)."""
+        capi.asfd_adjoint(self.handle, u1, grad_u2, grad_u1, grad_d1, self.shape1, self.shape2,
+                          stream)
+        return grad_u1, grad_d1
+
+    def __call__(self, u1: torch.Tensor, d1: torch.Tensor | None = None) -> torch.Tensor:
+        """Differentiable forward transform.  If d1 is given, the plan is
+        rebuilt for it first and gradients flow to it; gradients always flow
+        to u1.  The plan must not be updated between forward and backward."""
+        if d1 is not None:
+            self.update_d1(d1.detach())
+            return FresnelFunction.apply(u1, d1, self)
+        return FresnelFunction.apply(u1, None, self)
+
     def execute_host(self, u1: torch.Tensor, out: torch.Tensor, stream=None) -> torch.Tensor:
         capi.asfd_execute_host(self.handle, u1, out, self.shape1, self.shape2, stream)
         return out
@@ -81,3 +96,34 @@ class FresnelPlan:
             self.close()
         except Exception:
             pass
+
+
+class FresnelFunction(torch.autograd.Function):
+    """u2 = forward(u1; d1) with the type-2 adjoint as its backward.
+
+    PyTorch's complex-gradient convention (dL/dRe + i dL/dIm for a real loss)
+    is the one asfd_adjoint uses, so gradients pass through unchanged; the
+    d1 gradient is computed in FP32 and returned in d1's dtype."""
+
+    @staticmethod
+    def forward(ctx, u1, d1, plan):
+        u1c = u1.contiguous()
+        u2 = plan.execute(u1c)
+        ctx.plan = plan
+        ctx.has_d1 = d1 is not None
+        ctx.d1_dtype = d1.dtype if d1 is not None else None
+        ctx.save_for_backward(u1c)
+        return u2
+
+    @staticmethod
+    def backward(ctx, grad_u2):
+        (u1,) = ctx.saved_tensors
+        plan = ctx.plan
+        need_u1 = ctx.needs_input_grad[0]
+        need_d1 = ctx.has_d1 and ctx.needs_input_grad[1]
+        g2 = grad_u2.contiguous().to(torch.complex64)
+        gu1 = torch.empty_like(u1) if need_u1 else None
+        gd1 = torch.empty(plan.shape1, dtype=torch.float32, device=u1.device) if need_d1 else None
+        if need_u1 or need_d1:
+            plan.adjoint(u1 if need_d1 else None, g2, gu1, gd1)
+        return gu1, (gd1.to(ctx.d1_dtype) if need_d1 else None), None
