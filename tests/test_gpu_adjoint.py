@@ -137,14 +137,13 @@ def _fd_check(name, ncoord, seed):
         inten = (u2_t.abs() ** 2).double()
         target = torch.rand(inten.shape, generator=torch.Generator().manual_seed(seed),
                             dtype=torch.float64).to("cuda") * 2 * inten.mean()
-        gu2 = (4 * (inten - target) * u2_t.double()).to(torch.complex64)
+        gu2 = (4 * (inten - target) * u2_t.to(torch.complex128)).to(torch.complex64)
         gu1 = torch.empty_like(u1_t)
         gd1 = torch.empty(plan.shape1, dtype=torch.float32, device="cuda")
         plan.adjoint(u1_t, gu2, gu1, gd1)
         torch.cuda.synchronize()
     u2 = u2_t.cpu().numpy().astype(np.complex128)
     T = target.cpu().numpy()
-    I0 = np.abs(u2) ** 2
     gd1 = gd1.cpu().numpy().astype(np.float64)
     gu1 = gu1.cpu().numpy().astype(np.complex128)
     k = 2 * np.pi / g["lam"]
