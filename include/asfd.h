@@ -163,6 +163,46 @@ asfd_status asfd_execute_stage(asfd_plan plan, int stage, const float* u1_dev, f
 asfd_status asfd_adjoint(asfd_plan plan, const float* u1_dev, const float* grad_u2_dev,
                          float* grad_u1_dev, float* grad_d1_dev, void* stream);
 
+/*
+ * Learned spreading kernel (plans created with kind = ASFD_KERNEL_LEARNED and
+ * kernel_width = 4).  The ES kernel of the paper's NUFFT step is replaced by
+ * a narrower tabulated kernel: for every 16 x 16 block of source samples a
+ * small MLP maps dimensionless features of the block (position on the fine
+ * grid, local sample spacing, mean d1/(z0 - d1)) to a table of per-tap
+ * polynomials of degree 7 in the sample's sub-cell offset, added to a shared
+ * base table; the deconvolution is the width-4 ES one times a learned even
+ * Chebyshev correction.  The model is a flat vector of
+ * asfd_learned_param_count() floats (layout private to the library), trained
+ * on the GPU by asfd_learned_train_step.  asfd_execute, asfd_execute_stage
+ * and asfd_adjoint use the current model.
+ */
+
+/* Number of floats of the learned model. */
+size_t asfd_learned_param_count(void);
+
+/* Copy the model to host memory (count must equal asfd_learned_param_count()).
+ * Synchronous.  Errors: ASFD_ERR_ARG, ASFD_ERR_STATE (not a learned plan). */
+asfd_status asfd_learned_get_params(asfd_plan plan, float* params_host, size_t count);
+
+/* Load a model from host memory, reset the optimiser state and rebuild the
+ * tables; synchronises `stream`.  Errors: ASFD_ERR_ARG (count, non-finite
+ * values), ASFD_ERR_STATE. */
+asfd_status asfd_learned_set_params(asfd_plan plan, const float* params_host, size_t count,
+                                    void* stream);
+
+/*
+ * One Adam step (learning rate lr) on the relative squared error
+ * |u2 - ref|^2 / |ref|^2 of the forward transform of u1_dev against
+ * ref_u2_dev (device [m2y][m2x] complex, e.g. the ES-kernel transform at a
+ * large width, the judge of the learned kernel's error).  Runs the forward,
+ * the loss gradient, the adjoint FFT passes, the table, deconvolution and MLP
+ * gradients and the update on `stream`.  If loss_host is not NULL the loss
+ * before the update is written there (synchronises `stream`).
+ * Errors: ASFD_ERR_ARG, ASFD_ERR_STATE, ASFD_ERR_CUDA.
+ */
+asfd_status asfd_learned_train_step(asfd_plan plan, const float* u1_dev, const float* ref_u2_dev,
+                                    float lr, double* loss_host, void* stream);
+
 /* Fill *info.  Errors: ASFD_ERR_ARG. */
 asfd_status asfd_get_plan_info(asfd_plan plan, asfd_plan_info* info);
 

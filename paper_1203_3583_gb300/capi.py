@@ -82,6 +82,11 @@ SIGNATURES = {
     "asfd_status_string": (ctypes.c_char_p, [_int]),
     "asfd_last_error": (ctypes.c_char_p, []),
     "asfd_fft_lines": (_int, [_int, _int, _int, _vp, _vp, _vp]),
+    "asfd_learned_param_count": (ctypes.c_size_t, []),
+    "asfd_learned_get_params": (_int, [_vp, _vp, ctypes.c_size_t]),
+    "asfd_learned_set_params": (_int, [_vp, _vp, ctypes.c_size_t, _vp]),
+    "asfd_learned_train_step": (_int, [_vp, _vp, _vp, ctypes.c_float,
+                                       ctypes.POINTER(ctypes.c_double), _vp]),
 }
 
 _lock = threading.Lock()
@@ -213,3 +218,32 @@ def asfd_fft_lines(x: torch.Tensor, sign: int = -1, out: torch.Tensor | None = N
                                  _dev_ptr(out, torch.complex64, (lines, n), "out"),
                                  _stream(stream)))
     return out
+
+
+def asfd_learned_param_count() -> int:
+    return int(load().asfd_learned_param_count())
+
+
+def asfd_learned_get_params(plan):
+    import numpy as np
+    n = asfd_learned_param_count()
+    out = np.empty(n, np.float32)
+    _check(load().asfd_learned_get_params(plan, ctypes.c_void_p(out.ctypes.data), n))
+    return out
+
+
+def asfd_learned_set_params(plan, params, stream=None) -> None:
+    import numpy as np
+    p = np.ascontiguousarray(params, np.float32)
+    _check(load().asfd_learned_set_params(plan, ctypes.c_void_p(p.ctypes.data), p.size,
+                                          _stream(stream)))
+
+
+def asfd_learned_train_step(plan, u1, ref, lr, shape1, shape2, want_loss=True, stream=None):
+    loss = ctypes.c_double(0.0)
+    _check(load().asfd_learned_train_step(plan, _dev_ptr(u1, torch.complex64, shape1, "u1"),
+                                          _dev_ptr(ref, torch.complex64, shape2, "ref"),
+                                          ctypes.c_float(lr),
+                                          ctypes.byref(loss) if want_loss else None,
+                                          _stream(stream)))
+    return loss.value if want_loss else None

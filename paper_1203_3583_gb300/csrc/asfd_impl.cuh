@@ -20,6 +20,28 @@ constexpr int kSrcTile = 16;  // source tiles are kSrcTile x kSrcTile samples
 constexpr int kColTileY = 32; // rows of a tile of the conflict-free spreading kernel
 constexpr int kMaxRingWidth = 14;  // widest kernel of the conflict-free spreading path (no spills)
 
+// Learned spreading kernel: width kLearnW, per-source-tile polynomial of
+// degree kLearnDeg per tap and axis in t = 2 dx - 1, an MLP of kLearnFeat
+// inputs and kLearnHidden tanh units, and an even Chebyshev correction of
+// kLearnCheb terms per axis on the deconvolution.
+constexpr int kLearnW = 4;
+constexpr int kLearnDeg = 7;
+constexpr int kLearnCoef = kLearnDeg + 1;
+constexpr int kLearnTableSize = 2 * kLearnW * kLearnCoef;  // [axis][tap][coef]
+constexpr int kLearnFeat = 6;
+constexpr int kLearnHidden = 32;
+constexpr int kLearnCheb = 6;
+// parameter vector layout
+constexpr int kLpBase = 0;
+constexpr int kLpW1 = kLpBase + kLearnTableSize;
+constexpr int kLpB1 = kLpW1 + kLearnHidden * kLearnFeat;
+constexpr int kLpW2 = kLpB1 + kLearnHidden;
+constexpr int kLpB2 = kLpW2 + kLearnTableSize * kLearnHidden;
+constexpr int kLpDx = kLpB2 + kLearnTableSize;
+constexpr int kLpDy = kLpDx + kLearnCheb;
+constexpr int kLearnParams = kLpDy + kLearnCheb;
+constexpr float kLearnOutScale = 1e-3f;  // scale of the MLP's per-tile table correction
+
 // Device status word bits (set by kernels, read by asfd_check_device_status).
 constexpr unsigned kStatusBadD1 = 1u;       // non-finite d1 or d1 >= z0
 constexpr unsigned kStatusRange = 2u;       // |d1|/z0 above the supported bound
@@ -97,6 +119,24 @@ struct asfd_plan_s {
     float2* grid = nullptr;         // [nfy][nfx]
     float2* rows = nullptr;         // [nfy][m2x] row-FFT output (band rows first)
     unsigned* status = nullptr;     // device status word
+    // learned kernel (kind == ASFD_KERNEL_LEARNED)
+    bool learned = false;
+    float* ltab = nullptr;          // [source tiles][kLearnTableSize] current tables
+    float* lfeat = nullptr;         // [source tiles][kLearnFeat]
+    float* lhid = nullptr;          // [source tiles][kLearnHidden] hidden activations
+    float* ltgrad = nullptr;        // [source tiles][kLearnTableSize] dL/dtable
+    float* lparams = nullptr;       // [kLearnParams]
+    float* lgrad = nullptr;
+    float* lm = nullptr;            // Adam moments
+    float* lv = nullptr;
+    int lstep = 0;
+    float2* cxb = nullptr;          // base deconvolution/chirp tables (ES, width 4)
+    float2* cyb = nullptr;
+    float* lcorr = nullptr;         // [m2x + m2y] current deconvolution corrections
+    float* lcgrad = nullptr;        // [m2x + m2y] dL/dcorrection
+    float2* lu2 = nullptr;          // [m2y][m2x] training forward output
+    float2* lres = nullptr;         // [m2y][m2x] loss gradient
+    double* lred = nullptr;         // [2] loss reductions
     float2* stage_u1 = nullptr;     // staging for asfd_execute_host (allocated on first use)
     float2* stage_u2 = nullptr;
 
@@ -134,5 +174,12 @@ asfd_status plan_alloc(asfd_plan_s* P);
 asfd_status build_twiddles(float2* tw, int L, cudaStream_t st);
 asfd_status plan_build_tables(asfd_plan_s* P, cudaStream_t st);
 asfd_status plan_build_d1(asfd_plan_s* P, const double* d1, cudaStream_t st);
+asfd_status plan_alloc_buffer(asfd_plan_s* P, void** p, size_t bytes);
+// learned kernel
+asfd_status learned_init(asfd_plan_s* P, cudaStream_t st);
+asfd_status learned_refresh(asfd_plan_s* P, cudaStream_t st);   // features -> tables, deconvolution
+asfd_status learned_features(asfd_plan_s* P, cudaStream_t st);
+asfd_status learned_train_step(asfd_plan_s* P, const float2* u1, const float2* ref, float lr,
+                               double* loss_out, cudaStream_t st);
 
 }  // namespace asfd

@@ -1,5 +1,6 @@
 // The exported C ABI (include/asfd.h): argument checks, plan lifetime, and
 // the forward transform as three kernels on the caller's stream.
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -96,7 +97,13 @@ asfd_status asfd_plan_create(asfd_plan* out, const asfd_params* p, const double*
         if (r != ASFD_OK) return r;
         r = plan_build_tables(P, st);
         if (r != ASFD_OK) return r;
-        return plan_build_d1(P, d1_dev, st);
+        r = plan_build_d1(P, d1_dev, st);
+        if (r != ASFD_OK) return r;
+        if (p->kind == ASFD_KERNEL_LEARNED) {
+            P->learned = true;
+            return learned_init(P, st);
+        }
+        return ASFD_OK;
     }();
     if (s != ASFD_OK) {
         free_all(P);
@@ -254,6 +261,56 @@ asfd_status asfd_destroy(asfd_plan P)
     cudaSetDevice(prev);
     delete P;
     return ASFD_OK;
+}
+
+size_t asfd_learned_param_count(void) { return (size_t)kLearnParams; }
+
+asfd_status asfd_learned_get_params(asfd_plan P, float* params_host, size_t count)
+{
+    clear_error();
+    if (!P || !params_host) return fail(ASFD_ERR_ARG, "plan or params is NULL");
+    if (!P->learned) return fail(ASFD_ERR_STATE, "plan does not use the learned kernel");
+    if (count != (size_t)kLearnParams) return fail(ASFD_ERR_ARG, "count must equal asfd_learned_param_count()");
+    return on_device(P->device, [&]() -> asfd_status {
+        ASFD_CUDA(cudaMemcpy(params_host, P->lparams, sizeof(float) * kLearnParams, cudaMemcpyDeviceToHost));
+        return ASFD_OK;
+    });
+}
+
+asfd_status asfd_learned_set_params(asfd_plan P, const float* params_host, size_t count, void* stream)
+{
+    clear_error();
+    if (!P || !params_host) return fail(ASFD_ERR_ARG, "plan or params is NULL");
+    if (!P->learned) return fail(ASFD_ERR_STATE, "plan does not use the learned kernel");
+    if (count != (size_t)kLearnParams) return fail(ASFD_ERR_ARG, "count must equal asfd_learned_param_count()");
+    for (size_t i = 0; i < count; ++i)
+        if (!std::isfinite(params_host[i])) return fail(ASFD_ERR_ARG, "non-finite parameter");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    return on_device(P->device, [&]() -> asfd_status {
+        ASFD_CUDA(cudaMemcpyAsync(P->lparams, params_host, sizeof(float) * kLearnParams,
+                                  cudaMemcpyHostToDevice, st));
+        ASFD_CUDA(cudaMemsetAsync(P->lm, 0, sizeof(float) * kLearnParams, st));
+        ASFD_CUDA(cudaMemsetAsync(P->lv, 0, sizeof(float) * kLearnParams, st));
+        P->lstep = 0;
+        asfd_status s = learned_refresh(P, st);
+        if (s != ASFD_OK) return s;
+        ASFD_CUDA(cudaStreamSynchronize(st));
+        return ASFD_OK;
+    });
+}
+
+asfd_status asfd_learned_train_step(asfd_plan P, const float* u1_dev, const float* ref_u2_dev,
+                                    float lr, double* loss_host, void* stream)
+{
+    clear_error();
+    if (!P || !u1_dev || !ref_u2_dev) return fail(ASFD_ERR_ARG, "plan, u1 or ref is NULL");
+    if (!P->learned) return fail(ASFD_ERR_STATE, "plan does not use the learned kernel");
+    if (!(lr >= 0.f) || !std::isfinite(lr)) return fail(ASFD_ERR_ARG, "lr must be finite and >= 0");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    return on_device(P->device, [&]() -> asfd_status {
+        return learned_train_step(P, reinterpret_cast<const float2*>(u1_dev),
+                                  reinterpret_cast<const float2*>(ref_u2_dev), lr, loss_host, st);
+    });
 }
 
 asfd_status asfd_fft_lines(int n, int lines, int sign, const float* in_dev, float* out_dev,

@@ -317,6 +317,8 @@ bool pow2_in(int n, int lo, int hi) { return n >= lo && n <= hi && (n & (n - 1))
 
 asfd_status plan_build_colored(asfd_plan_s* P, bool wraps, cudaStream_t st);
 
+asfd_status plan_alloc_buffer(asfd_plan_s* P, void** p, size_t bytes) { return alloc(P, p, bytes); }
+
 asfd_status plan_validate(const asfd_params* p, int* nfx, int* nfy, double* beta)
 {
     if (!p) return fail(ASFD_ERR_ARG, "params is NULL");
@@ -331,8 +333,10 @@ asfd_status plan_validate(const asfd_params* p, int* nfx, int* nfy, double* beta
             return fail(ASFD_ERR_ARG, "pitches, wavelength, z0 and sigma must be finite and > 0");
     if (p->kernel_width < 2 || p->kernel_width > 16)
         return fail(ASFD_ERR_UNSUPPORTED, "kernel_width must be in [2, 16]");
-    if (p->kind != ASFD_KERNEL_ES)
-        return fail(ASFD_ERR_UNSUPPORTED, "only the ES kernel is available in this plan type");
+    if (p->kind != ASFD_KERNEL_ES && p->kind != ASFD_KERNEL_LEARNED)
+        return fail(ASFD_ERR_ARG, "kind must be ASFD_KERNEL_ES or ASFD_KERNEL_LEARNED");
+    if (p->kind == ASFD_KERNEL_LEARNED && p->kernel_width != kLearnW)
+        return fail(ASFD_ERR_UNSUPPORTED, "the learned kernel has width 4");
     if (!(p->sigma >= 1.25 && p->sigma <= 4.0))
         return fail(ASFD_ERR_UNSUPPORTED, "sigma must be in [1.25, 4]");
     const double fx = p->sigma * p->m2x, fy = p->sigma * p->m2y;
@@ -537,7 +541,14 @@ asfd_status plan_build_d1(asfd_plan_s* P, const double* d1, cudaStream_t st)
     P->band_ty1 = by1 + 1;
     P->tile_pairs = (long long)lst.size();
     P->max_abs_eps = me;
-    return plan_build_colored(P, wrapx || wrapy, st);
+    asfd_status cs = plan_build_colored(P, wrapx || wrapy, st);
+    if (cs != ASFD_OK) return cs;
+    if (P->learned && P->lfeat) {
+        cs = learned_features(P, st);
+        if (cs != ASFD_OK) return cs;
+        return learned_refresh(P, st);
+    }
+    return ASFD_OK;
 }
 
 // Decides whether the conflict-free spreading kernel applies and, if so,

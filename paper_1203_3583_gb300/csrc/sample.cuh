@@ -128,3 +128,39 @@ __device__ __forceinline__ void es_weight_deriv_fast(float z, float two_over_w, 
 }
 
 }  // namespace asfd
+
+namespace asfd {
+
+// Learned kernel weights: tap a of axis x is sum_k c[0][a][k] t^k with
+// t = 2 dx - 1 (monomials on [-1, 1], Horner), likewise y with dy.
+template <int W>
+__device__ __forceinline__ void table_weights(const float* tab, float dx, float dy, float (&wx)[W],
+                                              float (&wy)[W])
+{
+    static_assert(kLearnCoef == 8, "two float4 per polynomial");
+    const float4* t4 = reinterpret_cast<const float4*>(tab);
+    const float tx = fmaf(2.0f, dx, -1.0f), ty = fmaf(2.0f, dy, -1.0f);
+#pragma unroll
+    for (int i = 0; i < W; ++i) {
+        const float4 lo = __ldg(&t4[2 * i]), hi = __ldg(&t4[2 * i + 1]);
+        float p = hi.w;
+        p = fmaf(p, tx, hi.z);
+        p = fmaf(p, tx, hi.y);
+        p = fmaf(p, tx, hi.x);
+        p = fmaf(p, tx, lo.w);
+        p = fmaf(p, tx, lo.z);
+        p = fmaf(p, tx, lo.y);
+        wx[i] = fmaf(p, tx, lo.x);
+        const float4 lo2 = __ldg(&t4[2 * (W + i)]), hi2 = __ldg(&t4[2 * (W + i) + 1]);
+        float q = hi2.w;
+        q = fmaf(q, ty, hi2.z);
+        q = fmaf(q, ty, hi2.y);
+        q = fmaf(q, ty, hi2.x);
+        q = fmaf(q, ty, lo2.w);
+        q = fmaf(q, ty, lo2.z);
+        q = fmaf(q, ty, lo2.y);
+        wy[i] = fmaf(q, ty, lo2.x);
+    }
+}
+
+}  // namespace asfd

@@ -60,7 +60,26 @@ struct SpreadArgs {
     float half_w;      // w/2
     float beta_log2e;  // beta * log2(e)
     float two_over_w;  // 2/w
+    const float* table;  // learned kernel: per-source-tile polynomial tables (or NULL)
 };
+
+// Kernel weights of the W taps in x and y: the ES kernel, or the learned
+// per-source-tile polynomial table of the sample's source tile.
+template <int W, bool TAB>
+__device__ __forceinline__ void tap_weights(const SpreadArgs& a, int nx, int ny, float dx, float dy,
+                                            float (&wx)[W], float (&wy)[W])
+{
+    if constexpr (TAB) {
+        const int tile = (ny / kSrcTile) * a.nstx + nx / kSrcTile;
+        table_weights<W>(a.table + (size_t)tile * kLearnTableSize, dx, dy, wx, wy);
+    } else {
+#pragma unroll
+        for (int i = 0; i < W; ++i) {
+            wx[i] = es_weight_fast(dx + (float)i - a.half_w, a.two_over_w, a.beta_log2e);
+            wy[i] = es_weight_fast(dy + (float)i - a.half_w, a.two_over_w, a.beta_log2e);
+        }
+    }
+}
 
 // Conflict-free spreading: one warp per tile, plain shared-memory
 // read-modify-write.  Lanes form 4 row groups x 8 column groups; at step
@@ -70,7 +89,7 @@ struct SpreadArgs {
 // 49 taps of a lane are loaded, updated and stored as independent operations,
 // and a __syncwarp orders consecutive steps.  The inputs of the next step are
 // loaded while the current one is processed.
-template <int W, int TX, int TY>
+template <int W, int TX, int TY, bool TAB>
 __global__ void __launch_bounds__(32) spread_es_colored_kernel(SpreadArgs a)
 {
     constexpr int LD = TX + 4;  // padded row stride (complex slots)
@@ -114,13 +133,10 @@ __global__ void __launch_bounds__(32) spread_es_colored_kernel(SpreadArgs a)
                 if (cx > -W && cx < TX && cy > -W && cy < TY) {
                     const float2 c = sample_value_fast(cur);
                     float wx[W], wy[W];
+                    tap_weights<W, TAB>(a, nx0 + o, ny0 + j, dx, dy, wx, wy);
                     bool colok[W];
 #pragma unroll
-                    for (int i = 0; i < W; ++i) {
-                        wx[i] = es_weight_fast(dx + (float)i - a.half_w, a.two_over_w, a.beta_log2e);
-                        wy[i] = es_weight_fast(dy + (float)i - a.half_w, a.two_over_w, a.beta_log2e);
-                        colok[i] = (unsigned)(cx + i) < (unsigned)TX;
-                    }
+                    for (int i = 0; i < W; ++i) colok[i] = (unsigned)(cx + i) < (unsigned)TX;
                     // taps of this lane are distinct cells: load all, update, store all
                     float2* base = tile + cy * LD + cx;
                     float2 acc[W][W];
@@ -163,7 +179,7 @@ __global__ void __launch_bounds__(32) spread_es_colored_kernel(SpreadArgs a)
     }
 }
 
-template <int W>
+template <int W, bool TAB>
 __global__ void __launch_bounds__(256) spread_es_atomic_kernel(SpreadArgs a)
 {
     __shared__ float tre[kTileY * kTileX];
@@ -203,16 +219,23 @@ __global__ void __launch_bounds__(256) spread_es_atomic_kernel(SpreadArgs a)
         if (!(hitx && hity)) continue;
         const float2 c = sample_value(__ldg(&a.u1[n]), ex, ey, q);
 
-        float wx[W];
+        float wx[W], wyv[W];
+        if constexpr (TAB) {
+            tap_weights<W, true>(a, nx, ny, dx, dy, wx, wyv);
+        } else {
 #pragma unroll
-        for (int i = 0; i < W; ++i) wx[i] = es_weight(dx + (float)i - a.half_w, a.two_over_w, a.beta_log2e);
+            for (int i = 0; i < W; ++i) {
+                wx[i] = es_weight(dx + (float)i - a.half_w, a.two_over_w, a.beta_log2e);
+                wyv[i] = es_weight(dy + (float)i - a.half_w, a.two_over_w, a.beta_log2e);
+            }
+        }
 
 #pragma unroll
         for (int j = 0; j < W; ++j) {
             int row = cy0 + j;
             if (row > my) row -= a.nfy;
             if (row >= kTileY) continue;
-            const float wy = es_weight(dy + (float)j - a.half_w, a.two_over_w, a.beta_log2e);
+            const float wy = wyv[j];
             const float cr = c.x * wy, ci = c.y * wy;
             float* rre = tre + row * kTileX;
             float* rim = tim + row * kTileX;
@@ -241,15 +264,25 @@ __global__ void __launch_bounds__(256) spread_es_atomic_kernel(SpreadArgs a)
 template <int W>
 cudaError_t launch_w(const SpreadArgs& a, int tiles, bool colored, cudaStream_t st)
 {
-    // the W x W register window fits the register file up to W = kMaxRingWidth
+    // widths up to kMaxRingWidth compile without register spills
     if constexpr (W <= kMaxRingWidth) {
         if (colored) {
-            spread_es_colored_kernel<W, kTileX, kColTileY>
+            spread_es_colored_kernel<W, kTileX, kColTileY, false>
                 <<<tiles * (kTileY / kColTileY), 32, 0, st>>>(a);
             return cudaGetLastError();
         }
     }
-    spread_es_atomic_kernel<W><<<tiles, 256, 0, st>>>(a);
+    spread_es_atomic_kernel<W, false><<<tiles, 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_table(const SpreadArgs& a, int tiles, bool colored, cudaStream_t st)
+{
+    if (colored)
+        spread_es_colored_kernel<kLearnW, kTileX, kColTileY, true>
+            <<<tiles * (kTileY / kColTileY), 32, 0, st>>>(a);
+    else
+        spread_es_atomic_kernel<kLearnW, true><<<tiles, 256, 0, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -284,7 +317,13 @@ asfd_status launch_spread(asfd_plan_s* P, const float2* u1, cudaStream_t st)
     const int tiles = (P->band_tx1 - P->band_tx0) * (P->band_ty1 - P->band_ty0);
     if (tiles <= 0) return ASFD_OK;
     const bool colored = P->colored;
+    a.table = P->ltab;
     cudaError_t e;
+    if (P->learned) {
+        e = launch_table(a, tiles, colored, st);
+        if (e != cudaSuccess) return cuda_fail(e, "learned spread kernel launch");
+        return ASFD_OK;
+    }
     switch (P->w) {
         case 2: e = launch_w<2>(a, tiles, colored, st); break;
         case 3: e = launch_w<3>(a, tiles, colored, st); break;

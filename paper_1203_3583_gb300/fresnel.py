@@ -27,10 +27,16 @@ class FresnelPlan:
     """Plan for Eq. 8 of the paper on one GPU (see include/asfd.h)."""
 
     def __init__(self, geometry: dict, d1, sigma: float = 2.0, kernel_width: int = 7,
-                 es_beta: float = 0.0, stream=None):
+                 es_beta: float = 0.0, stream=None, kind: str = "es"):
         self.geometry = dict(geometry)
-        self.params = capi.make_params(geometry, sigma=sigma, kernel_width=kernel_width,
-                                       es_beta=es_beta)
+        if kind not in ("es", "learned"):
+            raise ValueError("kind must be 'es' or 'learned'")
+        self.kind = kind
+        if kind == "learned":
+            kernel_width = 4
+        self.params = capi.make_params(
+            geometry, sigma=sigma, kernel_width=kernel_width, es_beta=es_beta,
+            kind=capi.ASFD_KERNEL_LEARNED if kind == "learned" else capi.ASFD_KERNEL_ES)
         self.shape1 = (int(geometry["n1y"]), int(geometry["n1x"]))
         self.shape2 = (int(geometry["m2y"]), int(geometry["m2x"]))
         self._handle = None
