@@ -203,6 +203,28 @@ asfd_status asfd_learned_set_params(asfd_plan plan, const float* params_host, si
 asfd_status asfd_learned_train_step(asfd_plan plan, const float* u1_dev, const float* ref_u2_dev,
                                     float lr, double* loss_host, void* stream);
 
+/* Gradient of the same loss with respect to every model parameter (no
+ * update), copied to grad_host (count = asfd_learned_param_count()); the loss
+ * goes to loss_host if not NULL.  Synchronises `stream`.  For checking the
+ * training kernels against an independent CPU computation. */
+asfd_status asfd_learned_gradient(asfd_plan plan, const float* u1_dev, const float* ref_u2_dev,
+                                  float* grad_host, size_t count, double* loss_host, void* stream);
+
+/*
+ * Layout of the learned model vector (all float), an interface shared with
+ * tools that read or write models.  T = 64 table entries per tile, ordered
+ * [axis x, y][tap 0..3][power 0..7] of t = 2 dx - 1; F = 6 features
+ * (1, mean fine-grid x and y relative to the grid centre in units of nf/2,
+ * mean sample spacing on the fine grid minus 1 in x and y, 100 x mean
+ * d1/(z0 - d1)); H = 32 tanh hidden units; C = 6 even Chebyshev terms:
+ *   [0, 64)        base table (T)
+ *   [64, 256)      W1[H][F]            [256, 288)    b1[H]
+ *   [288, 2336)    W2[T][H]            [2336, 2400)  b2[T]
+ *   [2400, 2406)   d_x[C]              [2406, 2412)  d_y[C]
+ * table(tile) = base + 0.001 (W2 tanh(W1 f + b1) + b2); deconvolution factor
+ * per axis = (ES width-4 factor) x (1 + sum_j d_j T_{2j}(2 m'/M)), j = 1..C.
+ */
+
 /* Fill *info.  Errors: ASFD_ERR_ARG. */
 asfd_status asfd_get_plan_info(asfd_plan plan, asfd_plan_info* info);
 

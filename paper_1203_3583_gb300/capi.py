@@ -87,7 +87,22 @@ SIGNATURES = {
     "asfd_learned_set_params": (_int, [_vp, _vp, ctypes.c_size_t, _vp]),
     "asfd_learned_train_step": (_int, [_vp, _vp, _vp, ctypes.c_float,
                                        ctypes.POINTER(ctypes.c_double), _vp]),
+    "asfd_learned_gradient": (_int, [_vp, _vp, _vp, _vp, ctypes.c_size_t,
+                                     ctypes.POINTER(ctypes.c_double), _vp]),
 }
+
+
+def asfd_learned_gradient(plan, u1, ref, shape1, shape2, stream=None):
+    """(gradient as a float32 numpy vector, loss) of the learned model."""
+    import numpy as np
+    n = asfd_learned_param_count()
+    out = np.empty(n, np.float32)
+    loss = ctypes.c_double(0.0)
+    _check(load().asfd_learned_gradient(plan, _dev_ptr(u1, torch.complex64, shape1, "u1"),
+                                        _dev_ptr(ref, torch.complex64, shape2, "ref"),
+                                        ctypes.c_void_p(out.ctypes.data), n, ctypes.byref(loss),
+                                        _stream(stream)))
+    return out, loss.value
 
 _lock = threading.Lock()
 _lib = None

@@ -181,5 +181,7 @@ asfd_status learned_refresh(asfd_plan_s* P, cudaStream_t st);   // features -> t
 asfd_status learned_features(asfd_plan_s* P, cudaStream_t st);
 asfd_status learned_train_step(asfd_plan_s* P, const float2* u1, const float2* ref, float lr,
                                double* loss_out, cudaStream_t st);
+asfd_status learned_gradient(asfd_plan_s* P, const float2* u1, const float2* ref, cudaStream_t st);
+asfd_status learned_read_loss(asfd_plan_s* P, double* loss_out, cudaStream_t st);
 
 }  // namespace asfd

@@ -313,6 +313,26 @@ asfd_status asfd_learned_train_step(asfd_plan P, const float* u1_dev, const floa
     });
 }
 
+asfd_status asfd_learned_gradient(asfd_plan P, const float* u1_dev, const float* ref_u2_dev,
+                                  float* grad_host, size_t count, double* loss_host, void* stream)
+{
+    clear_error();
+    if (!P || !u1_dev || !ref_u2_dev || !grad_host) return fail(ASFD_ERR_ARG, "NULL argument");
+    if (!P->learned) return fail(ASFD_ERR_STATE, "plan does not use the learned kernel");
+    if (count != (size_t)kLearnParams) return fail(ASFD_ERR_ARG, "count must equal asfd_learned_param_count()");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    return on_device(P->device, [&]() -> asfd_status {
+        asfd_status s = learned_gradient(P, reinterpret_cast<const float2*>(u1_dev),
+                                         reinterpret_cast<const float2*>(ref_u2_dev), st);
+        if (s != ASFD_OK) return s;
+        ASFD_CUDA(cudaMemcpyAsync(grad_host, P->lgrad, sizeof(float) * kLearnParams,
+                                  cudaMemcpyDeviceToHost, st));
+        if (loss_host) return learned_read_loss(P, loss_host, st);
+        ASFD_CUDA(cudaStreamSynchronize(st));
+        return ASFD_OK;
+    });
+}
+
 asfd_status asfd_fft_lines(int n, int lines, int sign, const float* in_dev, float* out_dev,
                            void* stream)
 {

@@ -509,8 +509,9 @@ asfd_status learned_init(asfd_plan_s* P, cudaStream_t st)
     return ASFD_OK;
 }
 
-asfd_status learned_train_step(asfd_plan_s* P, const float2* u1, const float2* ref, float lr,
-                               double* loss_out, cudaStream_t st)
+// Forward with the current model, loss against `ref`, and every parameter
+// gradient into P->lgrad (no update).
+asfd_status learned_gradient(asfd_plan_s* P, const float2* u1, const float2* ref, cudaStream_t st)
 {
     const int nst = P->nstx * P->nsty;
     const int m2x = P->prm.m2x, m2y = P->prm.m2y;
@@ -556,6 +557,23 @@ asfd_status learned_train_step(asfd_plan_s* P, const float2* u1, const float2* r
     mlp_backward_kernel<<<nst < 256 ? nst : 256, 256, 0, st>>>(P->lparams, P->lfeat, P->lhid,
                                                                 P->ltgrad, nst, P->lgrad);
     ASFD_CUDA(cudaGetLastError());
+    return ASFD_OK;
+}
+
+asfd_status learned_read_loss(asfd_plan_s* P, double* loss_out, cudaStream_t st)
+{
+    double red[2];
+    ASFD_CUDA(cudaMemcpyAsync(red, P->lred, sizeof(red), cudaMemcpyDeviceToHost, st));
+    ASFD_CUDA(cudaStreamSynchronize(st));
+    *loss_out = red[0] / (red[1] > 0.0 ? red[1] : 1.0);
+    return ASFD_OK;
+}
+
+asfd_status learned_train_step(asfd_plan_s* P, const float2* u1, const float2* ref, float lr,
+                               double* loss_out, cudaStream_t st)
+{
+    asfd_status s = learned_gradient(P, u1, ref, st);
+    if (s != ASFD_OK) return s;
     // Adam
     ++P->lstep;
     const float b1 = 0.9f, b2 = 0.999f;
@@ -564,12 +582,7 @@ asfd_status learned_train_step(asfd_plan_s* P, const float2* u1, const float2* r
                                                            kLearnParams, lr, b1, b2, c1, c2, 1e-12f);
     ASFD_CUDA(cudaGetLastError());
     if ((s = learned_refresh(P, st)) != ASFD_OK) return s;
-    if (loss_out) {
-        double red[2];
-        ASFD_CUDA(cudaMemcpyAsync(red, P->lred, sizeof(red), cudaMemcpyDeviceToHost, st));
-        ASFD_CUDA(cudaStreamSynchronize(st));
-        *loss_out = red[0] / (red[1] > 0.0 ? red[1] : 1.0);
-    }
+    if (loss_out) return learned_read_loss(P, loss_out, st);
     return ASFD_OK;
 }
 
