@@ -225,6 +225,47 @@ asfd_status asfd_learned_gradient(asfd_plan plan, const float* u1_dev, const flo
  * per axis = (ES width-4 factor) x (1 + sum_j d_j T_{2j}(2 m'/M)), j = 1..C.
  */
 
+/*
+ * Batched transform of many surfaces (each with its own sizes, pitches,
+ * wavelength, distance and height map) in ONE persistent cooperative kernel
+ * per call, replayed through a CUDA graph: all spreads, a grid barrier, all
+ * row FFTs, a grid barrier, all column FFTs with deconvolution and chirp.
+ */
+typedef struct asfd_batch_s* asfd_batch;
+
+typedef struct {
+    int surfaces;
+    int blocks, threads_per_block;   /* persistent grid (all blocks co-resident)      */
+    int spread_items, row_items, col_items;
+    int graph;                       /* 1 when the launch runs from a CUDA graph      */
+    long long source_samples;        /* total over the batch                          */
+} asfd_batch_info;
+
+/*
+ * params[count], d1_devs[count] (host arrays; d1 device FP64 [n1y][n1x] each,
+ * read during the call).  All surfaces use the ES kernel with one common
+ * width in 4..8, fine grids up to 4096, and the conflict-free spread (a
+ * non-folding, non-wrapping map); otherwise ASFD_ERR_UNSUPPORTED.  Creates
+ * one plan per surface.  Errors as asfd_plan_create.
+ */
+asfd_status asfd_batch_create(asfd_batch* out, const asfd_params* params,
+                              const double* const* d1_devs, int count, void* stream);
+
+/*
+ * Transform every surface: u1_devs[i] (device [n1y][n1x] complex of surface
+ * i) -> u2_devs[i] (device [m2y][m2x] complex); host arrays of device
+ * pointers.  Synchronises `stream` first (the previous launch must have read
+ * the pointer table), then queues one graph launch.  Errors: ASFD_ERR_ARG,
+ * ASFD_ERR_CUDA.
+ */
+asfd_status asfd_batch_execute(asfd_batch batch, const float* const* u1_devs,
+                               float* const* u2_devs, void* stream);
+
+asfd_status asfd_batch_get_info(asfd_batch batch, asfd_batch_info* info);
+
+/* Release the batch and its plans (synchronises the device).  NULL accepted. */
+asfd_status asfd_batch_destroy(asfd_batch batch);
+
 /* Fill *info.  Errors: ASFD_ERR_ARG. */
 asfd_status asfd_get_plan_info(asfd_plan plan, asfd_plan_info* info);
 

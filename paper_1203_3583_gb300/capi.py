@@ -69,7 +69,22 @@ class PlanInfo(ctypes.Structure):
     ]
 
 
+class BatchInfo(ctypes.Structure):
+    """Mirror of asfd_batch_info."""
+
+    _fields_ = [
+        ("surfaces", ctypes.c_int), ("blocks", ctypes.c_int), ("threads_per_block", ctypes.c_int),
+        ("spread_items", ctypes.c_int), ("row_items", ctypes.c_int), ("col_items", ctypes.c_int),
+        ("graph", ctypes.c_int), ("source_samples", ctypes.c_longlong),
+    ]
+
+
 SIGNATURES = {
+    "asfd_batch_create": (_int, [ctypes.POINTER(_vp), ctypes.POINTER(Params),
+                                 ctypes.POINTER(_vp), _int, _vp]),
+    "asfd_batch_execute": (_int, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), _vp]),
+    "asfd_batch_get_info": (_int, [_vp, ctypes.POINTER(BatchInfo)]),
+    "asfd_batch_destroy": (_int, [_vp]),
     "asfd_plan_create": (_int, [ctypes.POINTER(_vp), ctypes.POINTER(Params), _vp, _vp]),
     "asfd_plan_update_d1": (_int, [_vp, _vp, _vp]),
     "asfd_execute": (_int, [_vp, _vp, _vp, _vp]),
@@ -90,6 +105,36 @@ SIGNATURES = {
     "asfd_learned_gradient": (_int, [_vp, _vp, _vp, _vp, ctypes.c_size_t,
                                      ctypes.POINTER(ctypes.c_double), _vp]),
 }
+
+
+def asfd_batch_create(params_list, d1_list, stream=None):
+    n = len(params_list)
+    arr = (Params * n)(*params_list)
+    ptrs = (_vp * n)(*[_dev_ptr(d, torch.float64, (p.n1y, p.n1x), "d1").value
+                       for p, d in zip(params_list, d1_list)])
+    out = ctypes.c_void_p()
+    _check(load().asfd_batch_create(ctypes.byref(out), arr, ptrs, n, _stream(stream)))
+    return out
+
+
+def asfd_batch_execute(batch, u1_list, u2_list, stream=None) -> None:
+    n = len(u1_list)
+    for t in list(u1_list) + list(u2_list):
+        if not (t.is_cuda and t.dtype == torch.complex64 and t.is_contiguous()):
+            raise TypeError("batch fields must be contiguous complex64 CUDA tensors")
+    p1 = (_vp * n)(*[t.data_ptr() for t in u1_list])
+    p2 = (_vp * n)(*[t.data_ptr() for t in u2_list])
+    _check(load().asfd_batch_execute(batch, p1, p2, _stream(stream)))
+
+
+def asfd_batch_get_info(batch) -> dict:
+    info = BatchInfo()
+    _check(load().asfd_batch_get_info(batch, ctypes.byref(info)))
+    return {name: getattr(info, name) for name, _ in BatchInfo._fields_}
+
+
+def asfd_batch_destroy(batch) -> None:
+    _check(load().asfd_batch_destroy(batch))
 
 
 def asfd_learned_gradient(plan, u1, ref, shape1, shape2, stream=None):

@@ -1,0 +1,389 @@
+// Batched transform: many surfaces (sizes, wavelengths and distances of
+// their own) in ONE persistent cooperative kernel, launched through a CUDA
+// graph.
+//
+// Each surface has its own plan (tables, binning, work buffers).  The kernel
+// runs stage-major over the whole batch:
+//   stage 0  every warp takes (surface, fine-grid tile) items of the
+//            conflict-free spread (8 warps per block, one tile each);
+//   grid barrier (cooperative groups: all blocks are co-resident, as the
+//            cooperative launch guarantees, so the barrier cannot deadlock);
+//   stage 1  every block takes (surface, row group) items of the row FFT;
+//   grid barrier;
+//   stage 2  every block takes (surface, column group) items of the column
+//            FFT with deconvolution and destination chirp.
+// Items of one stage are independent, so the only waits are the two grid
+// barriers of the CUDA runtime.  The per-surface argument blocks live in
+// device memory and are refreshed from a pinned host copy by a memcpy node of
+// the same graph, so one graph launch runs a whole batch for new field
+// pointers.
+#include <cooperative_groups.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "asfd_impl.cuh"
+#include "fft_items.cuh"
+#include "spread.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace asfd {
+
+namespace {
+
+constexpr int kBatchThreads = 256;
+constexpr int kBatchWarps = kBatchThreads / 32;
+constexpr int kBatchMaxNf = 4096;
+using BTile = ColoredTile<kTileX, kColTileY>;
+
+struct BatchSurf {
+    SpreadArgs sa;
+    RowArgs ra;
+    ColArgs ca;
+    int nfx, nfy;
+    int tile0, ntile;  // first item and count in the spread stage
+    int row0, nrow;    // row-pass items
+    int col0, ncol;    // column-pass items
+};
+
+// Surface owning item `it` of a stage (items are laid out surface by surface).
+template <int Which>
+__device__ __forceinline__ int owner(const BatchSurf* S, int n, int it)
+{
+    int s = 0;
+    for (int k = 1; k < n; ++k) {
+        const int start = Which == 0 ? S[k].tile0 : (Which == 1 ? S[k].row0 : S[k].col0);
+        if (it >= start) s = k;
+    }
+    return s;
+}
+
+template <int L>
+__device__ __forceinline__ void batch_row(const BatchSurf& s, int it, float2* sm, int tid)
+{
+    if constexpr (RowCfg<L>::THREADS == kBatchThreads) rows_body<L>(s.ra, it, sm, tid);
+}
+
+template <int L>
+__device__ __forceinline__ void batch_col(const BatchSurf& s, int it, float2* sm, int tid)
+{
+    constexpr int LPC = kBatchThreads / (L / 16);
+    if constexpr (LPC >= 1 && LPC * (L / 16) == kBatchThreads) cols_body<L, LPC>(s.ca, it, sm, tid);
+}
+
+template <int W>
+__global__ void __launch_bounds__(kBatchThreads) batch_kernel(const BatchSurf* __restrict__ S, int n,
+                                                              int ntile, int nrow, int ncol)
+{
+    extern __shared__ __align__(16) float2 sm[];
+    cg::grid_group grid = cg::this_grid();
+    const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
+
+    // stage 0: spread (warp items)
+    float2* wsm = sm + warp * BTile::SLOTS;
+    for (int it = blockIdx.x * kBatchWarps + warp; it < ntile; it += gridDim.x * kBatchWarps) {
+        const int s = owner<0>(S, n, it);
+        colored_tile<W, kTileX, kColTileY, false>(S[s].sa, it - S[s].tile0, wsm, lane);
+    }
+    grid.sync();
+
+    // stage 1: row FFT (block items; the item index is block-uniform)
+    for (int it = blockIdx.x; it < nrow; it += gridDim.x) {
+        const int s = owner<1>(S, n, it);
+        const BatchSurf& b = S[s];
+        switch (b.nfx) {
+            case 64: batch_row<64>(b, it - b.row0, sm, tid); break;
+            case 128: batch_row<128>(b, it - b.row0, sm, tid); break;
+            case 256: batch_row<256>(b, it - b.row0, sm, tid); break;
+            case 512: batch_row<512>(b, it - b.row0, sm, tid); break;
+            case 1024: batch_row<1024>(b, it - b.row0, sm, tid); break;
+            case 2048: batch_row<2048>(b, it - b.row0, sm, tid); break;
+            case 4096: batch_row<4096>(b, it - b.row0, sm, tid); break;
+            default: break;
+        }
+        __syncthreads();
+    }
+    grid.sync();
+
+    // stage 2: column FFT + deconvolution + destination chirp
+    for (int it = blockIdx.x; it < ncol; it += gridDim.x) {
+        const int s = owner<2>(S, n, it);
+        const BatchSurf& b = S[s];
+        switch (b.nfy) {
+            case 64: batch_col<64>(b, it - b.col0, sm, tid); break;
+            case 128: batch_col<128>(b, it - b.col0, sm, tid); break;
+            case 256: batch_col<256>(b, it - b.col0, sm, tid); break;
+            case 512: batch_col<512>(b, it - b.col0, sm, tid); break;
+            case 1024: batch_col<1024>(b, it - b.col0, sm, tid); break;
+            case 2048: batch_col<2048>(b, it - b.col0, sm, tid); break;
+            case 4096: batch_col<4096>(b, it - b.col0, sm, tid); break;
+            default: break;
+        }
+        __syncthreads();
+    }
+}
+
+size_t batch_smem_bytes()
+{
+    const size_t spread = sizeof(float2) * (size_t)BTile::SLOTS * kBatchWarps;
+    const size_t fft = RowCfg<kBatchMaxNf>::SMEM_BYTES;  // largest per-block FFT footprint
+    return std::max(spread, fft);
+}
+
+}  // namespace
+}  // namespace asfd
+
+struct asfd_batch_s {
+    std::vector<asfd_plan> plans;
+    int device = 0;
+    int width = 0;
+    asfd::BatchSurf* host = nullptr;  // pinned
+    asfd::BatchSurf* dev = nullptr;
+    int ntile = 0, nrow = 0, ncol = 0;
+    int grid_blocks = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    bool graph_ok = false;
+};
+
+namespace asfd {
+
+namespace {
+
+template <int W>
+cudaError_t launch_batch(asfd_batch_s* B, cudaStream_t st)
+{
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(batch_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)batch_smem_bytes());
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(B->grid_blocks);
+    cfg.blockDim = dim3(kBatchThreads);
+    cfg.dynamicSmemBytes = batch_smem_bytes();
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const BatchSurf* S = B->dev;
+    const int n = (int)B->plans.size();
+    return cudaLaunchKernelEx(&cfg, batch_kernel<W>, S, n, B->ntile, B->nrow, B->ncol);
+}
+
+cudaError_t launch_batch_w(asfd_batch_s* B, cudaStream_t st)
+{
+    switch (B->width) {
+        case 4: return launch_batch<4>(B, st);
+        case 5: return launch_batch<5>(B, st);
+        case 6: return launch_batch<6>(B, st);
+        case 7: return launch_batch<7>(B, st);
+        case 8: return launch_batch<8>(B, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <int W>
+cudaError_t batch_occupancy(int* blocks_per_sm)
+{
+    cudaError_t e = cudaFuncSetAttribute(batch_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)batch_smem_bytes());
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, batch_kernel<W>,
+                                                         kBatchThreads, batch_smem_bytes());
+}
+
+cudaError_t batch_occupancy_w(int w, int* blocks_per_sm)
+{
+    switch (w) {
+        case 4: return batch_occupancy<4>(blocks_per_sm);
+        case 5: return batch_occupancy<5>(blocks_per_sm);
+        case 6: return batch_occupancy<6>(blocks_per_sm);
+        case 7: return batch_occupancy<7>(blocks_per_sm);
+        case 8: return batch_occupancy<8>(blocks_per_sm);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+void batch_free(asfd_batch_s* B)
+{
+    if (B->exec) cudaGraphExecDestroy(B->exec);
+    if (B->graph) cudaGraphDestroy(B->graph);
+    if (B->dev) cudaFree(B->dev);
+    if (B->host) cudaFreeHost(B->host);
+    for (asfd_plan p : B->plans) asfd_destroy(p);
+    delete B;
+}
+
+}  // namespace
+}  // namespace asfd
+
+using namespace asfd;
+
+extern "C" {
+
+asfd_status asfd_batch_create(asfd_batch* out, const asfd_params* params,
+                              const double* const* d1_devs, int count, void* stream)
+{
+    clear_error();
+    if (!out || !params || !d1_devs || count <= 0)
+        return fail(ASFD_ERR_ARG, "out, params and d1 arrays must be non-NULL, count > 0");
+    *out = nullptr;
+    const int w = params[0].kernel_width;
+    for (int i = 0; i < count; ++i) {
+        if (params[i].kind != ASFD_KERNEL_ES || params[i].kernel_width != w)
+            return fail(ASFD_ERR_UNSUPPORTED, "a batch uses the ES kernel with one common width");
+        if (!d1_devs[i]) return fail(ASFD_ERR_ARG, "d1 pointer is NULL");
+    }
+    if (w < 4 || w > 8) return fail(ASFD_ERR_UNSUPPORTED, "batch kernel widths are 4..8");
+    asfd_batch_s* B = new (std::nothrow) asfd_batch_s();
+    if (!B) return fail(ASFD_ERR_NOMEM, "host allocation");
+    B->width = w;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    asfd_status s = [&]() -> asfd_status {
+        ASFD_CUDA(cudaGetDevice(&B->device));
+        for (int i = 0; i < count; ++i) {
+            asfd_plan p = nullptr;
+            asfd_status r = asfd_plan_create(&p, &params[i], d1_devs[i], stream);
+            if (r != ASFD_OK) return r;
+            B->plans.push_back(p);
+            if (!p->colored)
+                return fail(ASFD_ERR_UNSUPPORTED, "surface " + std::to_string(i) +
+                                                      " needs the atomic spreading kernel "
+                                                      "(folding or wrapping map)");
+            if (p->nfx > kBatchMaxNf || p->nfy > kBatchMaxNf)
+                return fail(ASFD_ERR_UNSUPPORTED, "batched fine grids are limited to 4096");
+        }
+        ASFD_CUDA(cudaMallocHost(&B->host, sizeof(BatchSurf) * count));
+        ASFD_CUDA(cudaMalloc(&B->dev, sizeof(BatchSurf) * count));
+        int nt = 0, nr = 0, nc = 0;
+        for (int i = 0; i < count; ++i) {
+            asfd_plan_s* P = B->plans[i];
+            BatchSurf& b = B->host[i];
+            b.sa = make_spread_args(P, nullptr);
+            b.ra = make_row_args(P);
+            b.ca = make_col_args(P, nullptr);
+            b.nfx = P->nfx;
+            b.nfy = P->nfy;
+            b.tile0 = nt;
+            b.ntile = (P->band_tx1 - P->band_tx0) * (P->band_ty1 - P->band_ty0) * (kTileY / kColTileY);
+            b.row0 = nr;
+            const int row_lpc = P->nfx >= 4096 ? 1 : 4096 / P->nfx;  // RowCfg<nfx>::LPC
+            b.nrow = (b.ra.nrows + row_lpc - 1) / row_lpc;
+            const int col_lpc = kBatchThreads / (P->nfy / 16);
+            b.col0 = nc;
+            b.ncol = (P->prm.m2x + col_lpc - 1) / col_lpc;
+            nt += b.ntile;
+            nr += b.nrow;
+            nc += b.ncol;
+        }
+        B->ntile = nt;
+        B->nrow = nr;
+        B->ncol = nc;
+        int per_sm = 0, sms = 0;
+        ASFD_CUDA(batch_occupancy_w(w, &per_sm));
+        ASFD_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, B->device));
+        if (per_sm < 1) return fail(ASFD_ERR_UNSUPPORTED, "batch kernel does not fit on an SM");
+        B->grid_blocks = per_sm * sms;
+        return ASFD_OK;
+    }();
+    if (s != ASFD_OK) {
+        batch_free(B);
+        return s;
+    }
+    (void)st;
+    *out = B;
+    return ASFD_OK;
+}
+
+asfd_status asfd_batch_execute(asfd_batch B, const float* const* u1_devs, float* const* u2_devs,
+                               void* stream)
+{
+    clear_error();
+    if (!B || !u1_devs || !u2_devs) return fail(ASFD_ERR_ARG, "NULL argument");
+    const int n = (int)B->plans.size();
+    for (int i = 0; i < n; ++i)
+        if (!u1_devs[i] || !u2_devs[i]) return fail(ASFD_ERR_ARG, "NULL field pointer");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int prev = 0;
+    ASFD_CUDA(cudaGetDevice(&prev));
+    if (prev != B->device) ASFD_CUDA(cudaSetDevice(B->device));
+    // the graph's memcpy node reads the pinned host table at launch time;
+    // wait until a previous launch has consumed it before rewriting it
+    ASFD_CUDA(cudaStreamSynchronize(st));
+    for (int i = 0; i < n; ++i) {
+        B->host[i].sa.u1 = reinterpret_cast<const float2*>(u1_devs[i]);
+        B->host[i].ca.u2 = reinterpret_cast<float2*>(u2_devs[i]);
+    }
+    asfd_status s = ASFD_OK;
+    if (!B->exec) {
+        // capture upload + cooperative launch once; fall back to direct
+        // launches if the runtime cannot capture the cooperative kernel
+        cudaStream_t cap = nullptr;
+        bool ok = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) == cudaSuccess;
+        if (ok) ok = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+        if (ok) {
+            cudaError_t e1 = cudaMemcpyAsync(B->dev, B->host, sizeof(BatchSurf) * n,
+                                             cudaMemcpyHostToDevice, cap);
+            cudaError_t e2 = launch_batch_w(B, cap);
+            cudaGraph_t g = nullptr;
+            cudaError_t e3 = cudaStreamEndCapture(cap, &g);
+            ok = e1 == cudaSuccess && e2 == cudaSuccess && e3 == cudaSuccess && g;
+            if (ok) ok = cudaGraphInstantiate(&B->exec, g, 0) == cudaSuccess;
+            if (ok) B->graph = g;
+            else if (g) cudaGraphDestroy(g);
+        }
+        if (cap) cudaStreamDestroy(cap);
+        cudaGetLastError();  // clear a failed capture
+        B->graph_ok = ok;
+        if (!ok) B->exec = nullptr;
+    }
+    if (B->graph_ok) {
+        cudaError_t e = cudaGraphLaunch(B->exec, st);
+        if (e != cudaSuccess) s = cuda_fail(e, "cudaGraphLaunch of the batch");
+    } else {
+        cudaError_t e = cudaMemcpyAsync(B->dev, B->host, sizeof(BatchSurf) * n,
+                                        cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = launch_batch_w(B, st);
+        if (e != cudaSuccess) s = cuda_fail(e, "batch kernel launch");
+    }
+    if (prev != B->device) cudaSetDevice(prev);
+    return s;
+}
+
+asfd_status asfd_batch_get_info(asfd_batch B, asfd_batch_info* info)
+{
+    clear_error();
+    if (!B || !info) return fail(ASFD_ERR_ARG, "NULL argument");
+    info->surfaces = (int)B->plans.size();
+    info->blocks = B->grid_blocks;
+    info->threads_per_block = kBatchThreads;
+    info->spread_items = B->ntile;
+    info->row_items = B->nrow;
+    info->col_items = B->ncol;
+    info->graph = B->graph_ok ? 1 : 0;
+    long long src = 0;
+    for (asfd_plan p : B->plans) src += (long long)p->prm.n1x * p->prm.n1y;
+    info->source_samples = src;
+    return ASFD_OK;
+}
+
+asfd_status asfd_batch_destroy(asfd_batch B)
+{
+    clear_error();
+    if (!B) return ASFD_OK;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(B->device);
+    cudaDeviceSynchronize();
+    batch_free(B);
+    cudaSetDevice(prev);
+    return ASFD_OK;
+}
+
+}  // extern "C"

@@ -14,82 +14,26 @@
 
 #include "asfd_impl.cuh"
 #include "fft.cuh"
+#include "fft_items.cuh"
 
 namespace asfd {
 
 namespace {
 
 template <int L>
-struct RowCfg {
-    static constexpr int TPL = L / 16;
-    static constexpr int LPC = L >= 4096 ? 1 : 4096 / L;  // lines per CTA
-    static constexpr int THREADS = TPL * LPC;
-    static constexpr int LS = FftShape<L>::SMEM + (TPL < 16 ? TPL : 0);
-    static constexpr size_t SMEM_BYTES = sizeof(float2) * LS * LPC;
-};
-
-template <int L>
-struct ColCfg {
-    static constexpr int TPL = L / 16;
-    static constexpr int LPC0 = (256 / TPL) > 4 ? (256 / TPL) : 4;
-    static constexpr int LPC = (LPC0 * TPL > 1024) ? (1024 / TPL) : LPC0;
-    static constexpr int THREADS = TPL * LPC;
-    static constexpr int LS = FftShape<L>::SMEM + 16 / (LPC < 16 ? LPC : 16);
-    static constexpr size_t SMEM_BYTES = sizeof(float2) * LS * LPC;
-};
-
-template <int L>
 __global__ void __launch_bounds__(RowCfg<L>::THREADS)
-fft_rows_kernel(const float2* __restrict__ grid, int row0, int nrows, int col_lo, int col_hi,
-                float2* __restrict__ out, int m2x, const float2* __restrict__ tw)
+fft_rows_kernel(RowArgs a)
 {
-    using C = RowCfg<L>;
     extern __shared__ float2 sm[];
-    const int line = threadIdx.x / C::TPL, t = threadIdx.x % C::TPL;
-    const int r = blockIdx.x * C::LPC + line;
-    const bool active = r < nrows;
-    const float2* src = grid + (size_t)(row0 + (active ? r : 0)) * L;
-    float2* dst = out + (size_t)(active ? r : 0) * m2x;
-    const int half = m2x / 2;
-    auto ld = [&](int i) -> float2 {
-        return (active && i >= col_lo && i < col_hi) ? __ldg(&src[i]) : make_float2(0.f, 0.f);
-    };
-    auto st = [&](int i, float2 v) {
-        if (!active) return;
-        if (i < half) dst[i + half] = v;
-        else if (i >= L - half) dst[i - (L - half)] = v;
-    };
-    fft_line<L, -1>(t, sm + line * C::LS, tw, ld, st);
+    rows_body<L>(a, blockIdx.x, sm, threadIdx.x);
 }
 
 template <int L>
 __global__ void __launch_bounds__(ColCfg<L>::THREADS)
-fft_cols_kernel(const float2* __restrict__ rows, int row0, int nrows, int m2x, int m2y,
-                const float2* __restrict__ cx, const float2* __restrict__ cy,
-                float2* __restrict__ u2, const float2* __restrict__ tw)
+fft_cols_kernel(ColArgs a)
 {
-    using C = ColCfg<L>;
     extern __shared__ float2 sm[];
-    const int c = threadIdx.x % C::LPC, t = threadIdx.x / C::LPC;
-    const int col = blockIdx.x * C::LPC + c;
-    const bool active = col < m2x;
-    const int colc = active ? col : 0;
-    const float2 fx = __ldg(&cx[colc]);
-    const int half = m2y / 2;
-    auto ld = [&](int i) -> float2 {
-        const int rr = i - row0;
-        return (active && rr >= 0 && rr < nrows) ? __ldg(&rows[(size_t)rr * m2x + colc])
-                                                 : make_float2(0.f, 0.f);
-    };
-    auto st = [&](int i, float2 v) {
-        if (!active) return;
-        int k;
-        if (i < half) k = i + half;
-        else if (i >= L - half) k = i - (L - half);
-        else return;
-        u2[(size_t)k * m2x + colc] = cmul(cmul(v, fx), __ldg(&cy[k]));
-    };
-    fft_line<L, -1>(t, sm + c * C::LS, tw, ld, st);
+    cols_body<L, ColCfg<L>::LPC>(a, blockIdx.x, sm, threadIdx.x);
 }
 
 // Adjoint column pass: h = conj(Cx Cy) gu2 placed at the kept bins, FFT with
@@ -177,32 +121,28 @@ cudaError_t set_smem(F* f, size_t bytes)
 }
 
 template <int L>
-cudaError_t rows_L(const float2* grid, int row0, int nrows, int col_lo, int col_hi, float2* out,
-                   int m2x, const float2* tw, cudaStream_t st)
+cudaError_t rows_L(const RowArgs& a, cudaStream_t st)
 {
     using C = RowCfg<L>;
     static std::once_flag once;
     static cudaError_t attr = cudaSuccess;
     std::call_once(once, [] { attr = set_smem(fft_rows_kernel<L>, C::SMEM_BYTES); });
     if (attr != cudaSuccess) return attr;
-    const int blocks = (nrows + C::LPC - 1) / C::LPC;
-    fft_rows_kernel<L><<<blocks, C::THREADS, C::SMEM_BYTES, st>>>(grid, row0, nrows, col_lo,
-                                                                  col_hi, out, m2x, tw);
+    const int blocks = (a.nrows + C::LPC - 1) / C::LPC;
+    fft_rows_kernel<L><<<blocks, C::THREADS, C::SMEM_BYTES, st>>>(a);
     return cudaGetLastError();
 }
 
 template <int L>
-cudaError_t cols_L(const float2* rows, int row0, int nrows, int m2x, int m2y, const float2* cx,
-                   const float2* cy, float2* u2, const float2* tw, cudaStream_t st)
+cudaError_t cols_L(const ColArgs& a, cudaStream_t st)
 {
     using C = ColCfg<L>;
     static std::once_flag once;
     static cudaError_t attr = cudaSuccess;
     std::call_once(once, [] { attr = set_smem(fft_cols_kernel<L>, C::SMEM_BYTES); });
     if (attr != cudaSuccess) return attr;
-    const int blocks = (m2x + C::LPC - 1) / C::LPC;
-    fft_cols_kernel<L><<<blocks, C::THREADS, C::SMEM_BYTES, st>>>(rows, row0, nrows, m2x, m2y,
-                                                                  cx, cy, u2, tw);
+    const int blocks = (a.m2x + C::LPC - 1) / C::LPC;
+    fft_cols_kernel<L><<<blocks, C::THREADS, C::SMEM_BYTES, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -277,14 +217,41 @@ __global__ void twiddle_kernel(float2* tw, int L)
 
 }  // namespace
 
+RowArgs make_row_args(const asfd_plan_s* P)
+{
+    RowArgs a;
+    a.grid = P->grid;
+    a.row0 = P->band_ty0 * kTileY;
+    a.nrows = (P->band_ty1 - P->band_ty0) * kTileY;
+    a.col_lo = P->band_tx0 * kTileX;
+    a.col_hi = P->band_tx1 * kTileX;
+    a.out = P->rows;
+    a.m2x = P->prm.m2x;
+    a.tw = P->twx;
+    return a;
+}
+
+ColArgs make_col_args(const asfd_plan_s* P, float2* u2)
+{
+    ColArgs a;
+    a.rows = P->rows;
+    a.row0 = P->band_ty0 * kTileY;
+    a.nrows = (P->band_ty1 - P->band_ty0) * kTileY;
+    a.m2x = P->prm.m2x;
+    a.m2y = P->prm.m2y;
+    a.cx = P->cx;
+    a.cy = P->cy;
+    a.u2 = u2;
+    a.tw = P->twy;
+    return a;
+}
+
 asfd_status launch_fft_rows(asfd_plan_s* P, cudaStream_t st)
 {
-    const int row0 = P->band_ty0 * kTileY;
-    const int nrows = (P->band_ty1 - P->band_ty0) * kTileY;
-    const int col_lo = P->band_tx0 * kTileX, col_hi = P->band_tx1 * kTileX;
-    if (nrows <= 0) return ASFD_OK;
+    const RowArgs a = make_row_args(P);
+    if (a.nrows <= 0) return ASFD_OK;
     cudaError_t e = cudaSuccess;
-#define ASFD_ROWS(L) e = rows_L<L>(P->grid, row0, nrows, col_lo, col_hi, P->rows, P->prm.m2x, P->twx, st)
+#define ASFD_ROWS(L) e = rows_L<L>(a, st)
     ASFD_FFT_SWITCH(P->nfx, ASFD_ROWS)
 #undef ASFD_ROWS
     if (e != cudaSuccess) return cuda_fail(e, "fft_rows_kernel launch");
@@ -293,10 +260,9 @@ asfd_status launch_fft_rows(asfd_plan_s* P, cudaStream_t st)
 
 asfd_status launch_fft_cols(asfd_plan_s* P, float2* u2, cudaStream_t st)
 {
-    const int row0 = P->band_ty0 * kTileY;
-    const int nrows = (P->band_ty1 - P->band_ty0) * kTileY;
+    const ColArgs a = make_col_args(P, u2);
     cudaError_t e = cudaSuccess;
-#define ASFD_COLS(L) e = cols_L<L>(P->rows, row0, nrows, P->prm.m2x, P->prm.m2y, P->cx, P->cy, u2, P->twy, st)
+#define ASFD_COLS(L) e = cols_L<L>(a, st)
     ASFD_FFT_SWITCH(P->nfy, ASFD_COLS)
 #undef ASFD_COLS
     if (e != cudaSuccess) return cuda_fail(e, "fft_cols_kernel launch");

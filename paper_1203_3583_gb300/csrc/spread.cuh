@@ -1,0 +1,164 @@
+// Spreading kernels shared by the per-plan launches and the batched
+// persistent kernel: the argument block, the kernel weights and the
+// conflict-free per-warp tile spread.  See spread.cu for the method.
+#pragma once
+
+#include "asfd_impl.cuh"
+#include "sample.cuh"
+
+namespace asfd {
+
+struct SpreadArgs {
+    const float2* u1;
+    const float* q;
+    const AxisEntry* ax;
+    const AxisEntry* ay;
+    const AxisPos* px;
+    const AxisPos* py;
+    const int* tile_off;
+    const int* tile_src;
+    const int4* tile_rect;
+    float2* grid;
+    int n1x, n1y;
+    int nfx, nfy;
+    int nstx;
+    int band_tx0, band_ty0, band_ntx;
+    int sx_min, h_min;
+    float half_w;      // w/2
+    float beta_log2e;  // beta * log2(e)
+    float two_over_w;  // 2/w
+    const float* table;  // learned kernel: per-source-tile polynomial tables (or NULL)
+};
+
+// Kernel weights of the W taps in x and y: the ES kernel, or the learned
+// per-source-tile polynomial table of the sample's source tile.
+template <int W, bool TAB>
+__device__ __forceinline__ void tap_weights(const SpreadArgs& a, int nx, int ny, float dx, float dy,
+                                            float (&wx)[W], float (&wy)[W])
+{
+    if constexpr (TAB) {
+        const int tile = (ny / kSrcTile) * a.nstx + nx / kSrcTile;
+        table_weights<W>(a.table + (size_t)tile * kLearnTableSize, dx, dy, wx, wy);
+    } else {
+#pragma unroll
+        for (int i = 0; i < W; ++i) {
+            wx[i] = es_weight_fast(dx + (float)i - a.half_w, a.two_over_w, a.beta_log2e);
+            wy[i] = es_weight_fast(dy + (float)i - a.half_w, a.two_over_w, a.beta_log2e);
+        }
+    }
+}
+
+// Conflict-free spreading: one warp per tile, plain shared-memory
+// read-modify-write.  Lanes form 4 row groups x 8 column groups; at step
+// (j, o) lane (lr, lc) takes sample (x0 + lc sx + o, y0 + lr h + j).  The
+// plan's strides make the footprints of the 32 samples of one step pairwise
+// disjoint (same row: sx columns apart, different rows: h rows apart), so the
+// 49 taps of a lane are loaded, updated and stored as independent operations,
+// and a __syncwarp orders consecutive steps.  The inputs of the next step are
+// loaded while the current one is processed.
+template <int TX, int TY>
+struct ColoredTile {
+    static constexpr int LD = TX + 4;  // padded row stride (complex slots)
+    static constexpr int SLOTS = TY * LD;
+};
+
+// One warp spreads every sample of tile t of the band (TX x TY cells) into
+// `tile` (ColoredTile<TX, TY>::SLOTS complex slots of shared memory) and
+// writes the tile to the fine grid.  All 32 lanes of the warp must call it.
+template <int W, int TX, int TY, bool TAB>
+__device__ __forceinline__ void colored_tile(const SpreadArgs& a, int t, float2* tile, int lane)
+{
+    constexpr int LD = ColoredTile<TX, TY>::LD;
+    const int ox = (a.band_tx0 + t % a.band_ntx) * TX;
+    const int oy = a.band_ty0 * kTileY + (t / a.band_ntx) * TY;
+
+    for (int i = lane; i < TY * LD; i += 32) tile[i] = make_float2(0.f, 0.f);
+    __syncwarp();
+
+    const int4 rc = a.tile_rect[t];  // [x, y) columns, [z, w) rows of source samples
+    const int rw = rc.y - rc.x, rh = rc.w - rc.z;
+    if (rw > 0 && rh > 0) {
+        const int lc = lane & 7, lr = lane >> 3;
+        const int sx = max(a.sx_min, (rw + 7) / 8);
+        const int h = max(a.h_min, (rh + 3) / 4);
+        const int nx0 = rc.x + lc * sx, ny0 = rc.z + lr * h;
+        const int steps = h * sx;
+        int j = 0, o = 0;
+        bool v = (nx0 < rc.y) && (ny0 < rc.w);
+        Raw cur;
+        if (v) cur = load_raw(a, nx0, ny0);
+        for (int k = 0; k < steps; ++k) {
+            // inputs of step k + 1
+            int j2 = j, o2 = o + 1;
+            if (o2 == sx) {
+                o2 = 0;
+                ++j2;
+            }
+            const bool v2 = (k + 1 < steps) && (nx0 + o2 < rc.y) && (ny0 + j2 < rc.w);
+            Raw nxt;
+            if (v2) nxt = load_raw(a, nx0 + o2, ny0 + j2);
+            if (v) {
+                int l0x, l0y;
+                float dx, dy;
+                sample_pos(cur.ex, cur.ey, cur.px, cur.py, cur.q, a.half_w, l0x, l0y, dx, dy);
+                const int cx = l0x - ox, cy = l0y - oy;
+                if (cx > -W && cx < TX && cy > -W && cy < TY) {
+                    const float2 c = sample_value_fast(cur);
+                    float wx[W], wy[W];
+                    tap_weights<W, TAB>(a, nx0 + o, ny0 + j, dx, dy, wx, wy);
+                    bool colok[W];
+#pragma unroll
+                    for (int i = 0; i < W; ++i) colok[i] = (unsigned)(cx + i) < (unsigned)TX;
+                    // taps of this lane are distinct cells: load all, update, store all
+                    float2* base = tile + cy * LD + cx;
+                    float2 acc[W][W];
+#pragma unroll
+                    for (int b = 0; b < W; ++b) {
+                        const bool rowok = (unsigned)(cy + b) < (unsigned)TY;
+#pragma unroll
+                        for (int i = 0; i < W; ++i)
+                            acc[b][i] = (rowok && colok[i]) ? base[b * LD + i] : make_float2(0.f, 0.f);
+                    }
+#pragma unroll
+                    for (int b = 0; b < W; ++b) {
+                        const float2 cb = make_float2(c.x * wy[b], c.y * wy[b]);
+#pragma unroll
+                        for (int i = 0; i < W; ++i) acc[b][i] = fma2(cb, wx[i], acc[b][i]);
+                    }
+#pragma unroll
+                    for (int b = 0; b < W; ++b) {
+                        const bool rowok = (unsigned)(cy + b) < (unsigned)TY;
+#pragma unroll
+                        for (int i = 0; i < W; ++i)
+                            if (rowok && colok[i]) base[b * LD + i] = acc[b][i];
+                    }
+                }
+            }
+            __syncwarp();
+            cur = nxt;
+            v = v2;
+            j = j2;
+            o = o2;
+        }
+    }
+    __syncwarp();
+
+    float4* g4 = reinterpret_cast<float4*>(a.grid);
+    for (int i = lane; i < TY * (TX / 2); i += 32) {
+        const int r = i / (TX / 2), c2 = i % (TX / 2);
+        const float2 v0 = tile[r * LD + 2 * c2], v1 = tile[r * LD + 2 * c2 + 1];
+        g4[((size_t)(oy + r) * a.nfx + ox) / 2 + c2] = make_float4(v0.x, v0.y, v1.x, v1.y);
+    }
+}
+
+template <int W, int TX, int TY, bool TAB>
+__global__ void __launch_bounds__(32) spread_es_colored_kernel(SpreadArgs a)
+{
+    __shared__ __align__(16) float2 tile[ColoredTile<TX, TY>::SLOTS];
+    colored_tile<W, TX, TY, TAB>(a, blockIdx.x, tile, threadIdx.x);
+}
+
+// Spread arguments of a plan for the field u1.
+SpreadArgs make_spread_args(const asfd_plan_s* P, const float2* u1);
+
+}  // namespace asfd

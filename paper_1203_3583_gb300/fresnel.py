@@ -104,6 +104,44 @@ class FresnelPlan:
             pass
 
 
+class FresnelBatch:
+    """Many surfaces in one persistent kernel per call (see asfd_batch_create)."""
+
+    def __init__(self, items, kernel_width: int = 7, sigma: float = 2.0, stream=None):
+        """items: list of (geometry, d1)."""
+        self.shapes1 = [(int(g["n1y"]), int(g["n1x"])) for g, _ in items]
+        self.shapes2 = [(int(g["m2y"]), int(g["m2x"])) for g, _ in items]
+        params = [capi.make_params(g, sigma=sigma, kernel_width=kernel_width) for g, _ in items]
+        d1s = [_as_cuda_f64(d1) for _, d1 in items]
+        self._handle = capi.asfd_batch_create(params, d1s, stream)
+
+    def execute(self, u1_list, out=None, stream=None):
+        if out is None:
+            out = [torch.empty(s, dtype=torch.complex64, device="cuda") for s in self.shapes2]
+        capi.asfd_batch_execute(self._handle, u1_list, out, stream)
+        return out
+
+    def info(self) -> dict:
+        return capi.asfd_batch_get_info(self._handle)
+
+    def close(self) -> None:
+        if self._handle is not None:
+            capi.asfd_batch_destroy(self._handle)
+            self._handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class FresnelFunction(torch.autograd.Function):
     """u2 = forward(u1; d1) with the type-2 adjoint as its backward.
 

@@ -66,7 +66,7 @@ class LearnedModel:
         return cls(z["params"], meta)
 
 
-def train_model(pairs, refs=None, steps=400, lr=2e-4, lr_final=2e-5, plan=None, log=None):
+def train_model(pairs, refs=None, steps=2000, lr=1e-2, lr_final=3.3e-4, plan=None, log=None):
     """Adam on the relative squared error against the reference fields,
     cycling over the pairs (the plan is rebuilt when the surface changes).
     lr decays geometrically from `lr` to `lr_final`.  Returns (model, losses)."""

@@ -106,8 +106,8 @@ def test_learned_gradient_matches_cpu_finite_differences():
 
 
 def test_trained_model_beats_es_at_width_4():
-    pairs = L.train_set(surfaces=2, fields=2, seed=300)
-    model, losses = L.train_model(pairs, steps=600, lr=1e-2, lr_final=3e-4)
+    pairs = L.train_set(surfaces=4, fields=2, seed=300)
+    model, losses = L.train_model(pairs)
     assert math.sqrt(losses[-1]) < math.sqrt(losses[0])
     g, u1, d1 = L.train_set(surfaces=1, fields=1, seed=700)[0]
     pts = W.sample_points(g, 512, seed=701)
@@ -119,4 +119,4 @@ def test_trained_model_beats_es_at_width_4():
         es4 = p.execute(torch.as_tensor(u1, device="cuda")).cpu().numpy()[pts[1], pts[0]]
     e_learned = np.linalg.norm(lw - ref) / np.linalg.norm(ref)
     e_es4 = np.linalg.norm(es4 - ref) / np.linalg.norm(ref)
-    assert e_learned < 0.75 * e_es4, (e_learned, e_es4)
+    assert e_learned < 0.7 * e_es4, (e_learned, e_es4)
