@@ -244,9 +244,11 @@ typedef struct {
 /*
  * params[count], d1_devs[count] (host arrays; d1 device FP64 [n1y][n1x] each,
  * read during the call).  All surfaces use the ES kernel with one common
- * width in 4..8, fine grids up to 4096, and the conflict-free spread (a
- * non-folding, non-wrapping map); otherwise ASFD_ERR_UNSUPPORTED.  Creates
- * one plan per surface.  Errors as asfd_plan_create.
+ * width in 4..8 and fine grids up to 4096; otherwise ASFD_ERR_UNSUPPORTED.
+ * Surfaces whose plan takes the atomic spreading kernel (folding, wrapping or
+ * very densely packed samples) are spread by whole blocks, the others by
+ * single warps, in the same launch.  Creates one plan per surface.  Errors as
+ * asfd_plan_create.
  */
 asfd_status asfd_batch_create(asfd_batch* out, const asfd_params* params,
                               const double* const* d1_devs, int count, void* stream);

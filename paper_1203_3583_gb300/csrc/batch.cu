@@ -20,6 +20,7 @@
 #include <cooperative_groups.h>
 
 #include <algorithm>
+#include <string>
 #include <vector>
 
 #include "asfd_impl.cuh"
@@ -42,7 +43,8 @@ struct BatchSurf {
     RowArgs ra;
     ColArgs ca;
     int nfx, nfy;
-    int tile0, ntile;  // first item and count in the spread stage
+    int tile0, ntile;  // first item and count of conflict-free (warp) spread tiles
+    int atile0, natile;  // first item and count of atomic (block) spread tiles
     int row0, nrow;    // row-pass items
     int col0, ncol;    // column-pass items
 };
@@ -53,7 +55,10 @@ __device__ __forceinline__ int owner(const BatchSurf* S, int n, int it)
 {
     int s = 0;
     for (int k = 1; k < n; ++k) {
-        const int start = Which == 0 ? S[k].tile0 : (Which == 1 ? S[k].row0 : S[k].col0);
+        const int start = Which == 0   ? S[k].tile0
+                          : Which == 1 ? S[k].row0
+                          : Which == 2 ? S[k].col0
+                                       : S[k].atile0;
         if (it >= start) s = k;
     }
     return s;
@@ -74,13 +79,24 @@ __device__ __forceinline__ void batch_col(const BatchSurf& s, int it, float2* sm
 
 template <int W>
 __global__ void __launch_bounds__(kBatchThreads) batch_kernel(const BatchSurf* __restrict__ S, int n,
-                                                              int ntile, int nrow, int ncol)
+                                                              int ntile, int natile, int nrow,
+                                                              int ncol)
 {
     extern __shared__ __align__(16) float2 sm[];
     cg::grid_group grid = cg::this_grid();
     const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
 
-    // stage 0: spread (warp items)
+    // stage 0a: spread of surfaces that need the atomic kernel (block items)
+    float* tre = reinterpret_cast<float*>(sm);
+    float* tim = tre + kTileX * kTileY;
+    for (int it = blockIdx.x; it < natile; it += gridDim.x) {
+        const int s = owner<3>(S, n, it);
+        atomic_tile<W, false>(S[s].sa, it - S[s].atile0, tre, tim, tid, kBatchThreads);
+        __syncthreads();
+    }
+    __syncthreads();
+
+    // stage 0b: conflict-free spread (warp items)
     float2* wsm = sm + warp * BTile::SLOTS;
     for (int it = blockIdx.x * kBatchWarps + warp; it < ntile; it += gridDim.x * kBatchWarps) {
         const int s = owner<0>(S, n, it);
@@ -127,8 +143,9 @@ __global__ void __launch_bounds__(kBatchThreads) batch_kernel(const BatchSurf* _
 size_t batch_smem_bytes()
 {
     const size_t spread = sizeof(float2) * (size_t)BTile::SLOTS * kBatchWarps;
+    const size_t atomic = 2 * sizeof(float) * kTileX * kTileY;
     const size_t fft = RowCfg<kBatchMaxNf>::SMEM_BYTES;  // largest per-block FFT footprint
-    return std::max(spread, fft);
+    return std::max(std::max(spread, atomic), fft);
 }
 
 }  // namespace
@@ -140,7 +157,7 @@ struct asfd_batch_s {
     int width = 0;
     asfd::BatchSurf* host = nullptr;  // pinned
     asfd::BatchSurf* dev = nullptr;
-    int ntile = 0, nrow = 0, ncol = 0;
+    int ntile = 0, natile = 0, nrow = 0, ncol = 0;
     int grid_blocks = 0;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -173,7 +190,7 @@ cudaError_t launch_batch(asfd_batch_s* B, cudaStream_t st)
     cfg.numAttrs = 1;
     const BatchSurf* S = B->dev;
     const int n = (int)B->plans.size();
-    return cudaLaunchKernelEx(&cfg, batch_kernel<W>, S, n, B->ntile, B->nrow, B->ncol);
+    return cudaLaunchKernelEx(&cfg, batch_kernel<W>, S, n, B->ntile, B->natile, B->nrow, B->ncol);
 }
 
 cudaError_t launch_batch_w(asfd_batch_s* B, cudaStream_t st)
@@ -252,16 +269,12 @@ asfd_status asfd_batch_create(asfd_batch* out, const asfd_params* params,
             asfd_status r = asfd_plan_create(&p, &params[i], d1_devs[i], stream);
             if (r != ASFD_OK) return r;
             B->plans.push_back(p);
-            if (!p->colored)
-                return fail(ASFD_ERR_UNSUPPORTED, "surface " + std::to_string(i) +
-                                                      " needs the atomic spreading kernel "
-                                                      "(folding or wrapping map)");
             if (p->nfx > kBatchMaxNf || p->nfy > kBatchMaxNf)
                 return fail(ASFD_ERR_UNSUPPORTED, "batched fine grids are limited to 4096");
         }
         ASFD_CUDA(cudaMallocHost(&B->host, sizeof(BatchSurf) * count));
         ASFD_CUDA(cudaMalloc(&B->dev, sizeof(BatchSurf) * count));
-        int nt = 0, nr = 0, nc = 0;
+        int nt = 0, na = 0, nr = 0, nc = 0;
         for (int i = 0; i < count; ++i) {
             asfd_plan_s* P = B->plans[i];
             BatchSurf& b = B->host[i];
@@ -270,8 +283,11 @@ asfd_status asfd_batch_create(asfd_batch* out, const asfd_params* params,
             b.ca = make_col_args(P, nullptr);
             b.nfx = P->nfx;
             b.nfy = P->nfy;
+            const int band_tiles = (P->band_tx1 - P->band_tx0) * (P->band_ty1 - P->band_ty0);
             b.tile0 = nt;
-            b.ntile = (P->band_tx1 - P->band_tx0) * (P->band_ty1 - P->band_ty0) * (kTileY / kColTileY);
+            b.ntile = P->colored ? band_tiles * (kTileY / kColTileY) : 0;
+            b.atile0 = na;
+            b.natile = P->colored ? 0 : band_tiles;
             b.row0 = nr;
             const int row_lpc = P->nfx >= 4096 ? 1 : 4096 / P->nfx;  // RowCfg<nfx>::LPC
             b.nrow = (b.ra.nrows + row_lpc - 1) / row_lpc;
@@ -279,22 +295,28 @@ asfd_status asfd_batch_create(asfd_batch* out, const asfd_params* params,
             b.col0 = nc;
             b.ncol = (P->prm.m2x + col_lpc - 1) / col_lpc;
             nt += b.ntile;
+            na += b.natile;
             nr += b.nrow;
             nc += b.ncol;
         }
         B->ntile = nt;
+        B->natile = na;
         B->nrow = nr;
         B->ncol = nc;
         int per_sm = 0, sms = 0;
         ASFD_CUDA(batch_occupancy_w(w, &per_sm));
         ASFD_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, B->device));
-        if (per_sm < 1) return fail(ASFD_ERR_UNSUPPORTED, "batch kernel does not fit on an SM");
+        if (per_sm < 1)
+            return fail(ASFD_ERR_UNSUPPORTED, "batch kernel does not fit on an SM (" +
+                                                  std::to_string(batch_smem_bytes()) +
+                                                  " bytes of shared memory)");
         B->grid_blocks = per_sm * sms;
         return ASFD_OK;
     }();
     if (s != ASFD_OK) {
+        const std::string msg = asfd_last_error();  // batch_free's plan destroys clear it
         batch_free(B);
-        return s;
+        return fail(s, msg);
     }
     (void)st;
     *out = B;
@@ -363,7 +385,7 @@ asfd_status asfd_batch_get_info(asfd_batch B, asfd_batch_info* info)
     info->surfaces = (int)B->plans.size();
     info->blocks = B->grid_blocks;
     info->threads_per_block = kBatchThreads;
-    info->spread_items = B->ntile;
+    info->spread_items = B->ntile + B->natile;
     info->row_items = B->nrow;
     info->col_items = B->ncol;
     info->graph = B->graph_ok ? 1 : 0;

@@ -594,7 +594,9 @@ asfd_status plan_build_colored(asfd_plan_s* P, bool wraps, cudaStream_t st)
     if (wraps || !(msx > 1e-3) || !(msy > 1e-3) || P->w > kMaxRingWidth) return ASFD_OK;
     const double sxd = std::ceil((P->w + margin) / msx);
     const double hd = std::ceil((P->w + spread_y + margin) / msy);
-    if (!(sxd <= 256.0) || !(hd <= 256.0)) return ASFD_OK;
+    // beyond 64 samples between lanes (samples packed far below one cell
+    // apart) few lanes find work in a tile and the atomic kernel is faster
+    if (!(sxd <= 64.0) || !(hd <= 64.0)) return ASFD_OK;
 
     // per band tile: source columns whose x range meets the tile's x range
     // widened by half a kernel and a cell, likewise rows (ranges are

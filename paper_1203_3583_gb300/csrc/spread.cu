@@ -45,81 +45,7 @@ __global__ void __launch_bounds__(256) spread_es_atomic_kernel(SpreadArgs a)
 {
     __shared__ float tre[kTileY * kTileX];
     __shared__ float tim[kTileY * kTileX];
-
-    const int tile = blockIdx.x;
-    const int ty = a.band_ty0 + tile / a.band_ntx;
-    const int tx = a.band_tx0 + tile % a.band_ntx;
-    const int ox = tx * kTileX, oy = ty * kTileY;
-
-    for (int i = threadIdx.x; i < kTileX * kTileY; i += blockDim.x) {
-        tre[i] = 0.f;
-        tim[i] = 0.f;
-    }
-    __syncthreads();
-
-    const int beg = a.tile_off[tile], end = a.tile_off[tile + 1];
-    const int total = (end - beg) * (kSrcTile * kSrcTile);
-    const int mx = a.nfx - 1, my = a.nfy - 1;
-    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-        const int s = a.tile_src[beg + idx / (kSrcTile * kSrcTile)];
-        const int local = idx % (kSrcTile * kSrcTile);
-        const int nx = (s % a.nstx) * kSrcTile + local % kSrcTile;
-        const int ny = (s / a.nstx) * kSrcTile + local / kSrcTile;
-        if (nx >= a.n1x || ny >= a.n1y) continue;
-        const size_t n = (size_t)ny * a.n1x + nx;
-        const float q = __ldg(&a.q[n]);
-        const AxisEntry ex = a.ax[nx], ey = a.ay[ny];
-        const AxisPos px = a.px[nx], py = a.py[ny];
-        int l0x, l0y;
-        float dx, dy;
-        sample_pos(ex, ey, px, py, q, a.half_w, l0x, l0y, dx, dy);
-        const int cx0 = (l0x - ox) & mx;  // tile-relative, wrapped to [0, nf)
-        const int cy0 = (l0y - oy) & my;
-        const bool hitx = (cx0 < kTileX) || (cx0 + W - 1 > mx);
-        const bool hity = (cy0 < kTileY) || (cy0 + W - 1 > my);
-        if (!(hitx && hity)) continue;
-        const float2 c = sample_value(__ldg(&a.u1[n]), ex, ey, q);
-
-        float wx[W], wyv[W];
-        if constexpr (TAB) {
-            tap_weights<W, true>(a, nx, ny, dx, dy, wx, wyv);
-        } else {
-#pragma unroll
-            for (int i = 0; i < W; ++i) {
-                wx[i] = es_weight(dx + (float)i - a.half_w, a.two_over_w, a.beta_log2e);
-                wyv[i] = es_weight(dy + (float)i - a.half_w, a.two_over_w, a.beta_log2e);
-            }
-        }
-
-#pragma unroll
-        for (int j = 0; j < W; ++j) {
-            int row = cy0 + j;
-            if (row > my) row -= a.nfy;
-            if (row >= kTileY) continue;
-            const float wy = wyv[j];
-            const float cr = c.x * wy, ci = c.y * wy;
-            float* rre = tre + row * kTileX;
-            float* rim = tim + row * kTileX;
-#pragma unroll
-            for (int i = 0; i < W; ++i) {
-                int col = cx0 + i;
-                if (col > mx) col -= a.nfx;
-                if (col >= kTileX) continue;
-                atomicAdd(rre + col, cr * wx[i]);
-                atomicAdd(rim + col, ci * wx[i]);
-            }
-        }
-    }
-    __syncthreads();
-
-    // write the tile (two cells per float4)
-    float4* g4 = reinterpret_cast<float4*>(a.grid);
-    for (int i = threadIdx.x; i < kTileX * kTileY / 2; i += blockDim.x) {
-        const int r = i / (kTileX / 2), c2 = i % (kTileX / 2);
-        const int l = r * kTileX + 2 * c2;
-        const size_t o = ((size_t)(oy + r) * a.nfx + ox) / 2 + c2;
-        g4[o] = make_float4(tre[l], tim[l], tre[l + 1], tim[l + 1]);
-    }
+    atomic_tile<W, TAB>(a, blockIdx.x, tre, tim, threadIdx.x, blockDim.x);
 }
 
 template <int W>
