@@ -63,8 +63,10 @@ def test_batch_equals_individual_plans(rgb_batch):
         with FresnelPlan(g, d1) as p:
             ref = p.execute(torch.as_tensor(u1, device="cuda")).cpu().numpy()
             ref_b = p.execute(torch.as_tensor(u1b[i], device="cuda")).cpu().numpy()
-        assert rel_l2(out[i], ref) < 1e-6, i
-        assert rel_l2(out_b[i], ref_b) < 1e-6, i
+        # identical arithmetic except the order of shared-memory float atomics
+        # (surfaces on the atomic spreading path) and FFT line grouping
+        assert rel_l2(out[i], ref) < 5e-6, i
+        assert rel_l2(out_b[i], ref_b) < 5e-6, i
 
 
 def test_batch_matches_oracle(rgb_batch):
