@@ -296,6 +296,28 @@ const char* asfd_last_error(void);
 asfd_status asfd_fft_lines(int n, int lines, int sign, const float* in_dev, float* out_dev,
                            void* stream);
 
+/*
+ * asfd_fft_lines without any device allocation (the paper has no
+ * counterpart; this is a service of the library).  For callers that cannot
+ * call cudaMalloc -- e.g. code whose device memory is all handed out up front
+ * by a host framework, or latency-critical loops that must avoid the
+ * implicit synchronisation of allocation calls -- this variant keeps its
+ * twiddle table in a fixed array compiled into the library (16384 complex
+ * values, 128 KiB on every GPU that loads the library, held until the
+ * process exits) instead of memory allocated on first use.
+ *   n: power of two in [16, 16384]; larger n is rejected with ASFD_ERR_ARG
+ *      and a message naming the limit.  Other arguments and the result are
+ *      exactly as for asfd_fft_lines.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  Every call on a device shares the one array
+ * and rewrites the n entries it reads before its transform, so calls that
+ * can overlap on the GPU (different streams, or different host threads on
+ * one device) race on the table and must be serialised by the caller.
+ */
+asfd_status asfd_fft_lines_noalloc(int n, int lines, int sign, const float* in_dev, float* out_dev,
+                                   void* stream);
+
 #ifdef __cplusplus
 }
 #endif

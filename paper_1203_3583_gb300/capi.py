@@ -97,6 +97,7 @@ SIGNATURES = {
     "asfd_status_string": (ctypes.c_char_p, [_int]),
     "asfd_last_error": (ctypes.c_char_p, []),
     "asfd_fft_lines": (_int, [_int, _int, _int, _vp, _vp, _vp]),
+    "asfd_fft_lines_noalloc": (_int, [_int, _int, _int, _vp, _vp, _vp]),
     "asfd_learned_param_count": (ctypes.c_size_t, []),
     "asfd_learned_get_params": (_int, [_vp, _vp, ctypes.c_size_t]),
     "asfd_learned_set_params": (_int, [_vp, _vp, ctypes.c_size_t, _vp]),
@@ -105,6 +106,21 @@ SIGNATURES = {
     "asfd_learned_gradient": (_int, [_vp, _vp, _vp, _vp, ctypes.c_size_t,
                                      ctypes.POINTER(ctypes.c_double), _vp]),
 }
+
+
+def asfd_fft_lines_noalloc(x: torch.Tensor, sign: int = -1, out: torch.Tensor | None = None,
+                           stream=None) -> torch.Tensor:
+    """asfd_fft_lines without device allocation inside the library (for
+    callers that cannot allocate; the twiddle table is a fixed 128 KiB array
+    of the library, shared by all calls on a device)."""
+    lines, n = x.shape
+    if out is None:
+        out = torch.empty_like(x)
+    _check(load().asfd_fft_lines_noalloc(n, lines, sign,
+                                         _dev_ptr(x, torch.complex64, (lines, n), "x"),
+                                         _dev_ptr(out, torch.complex64, (lines, n), "out"),
+                                         _stream(stream)))
+    return out
 
 
 def asfd_batch_create(params_list, d1_list, stream=None):

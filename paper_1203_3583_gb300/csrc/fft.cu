@@ -303,6 +303,23 @@ asfd_status build_twiddles(float2* tw, int L, cudaStream_t st)
     return ASFD_OK;
 }
 
+asfd_status launch_fft_lines_tw(int n, int lines, int sign, const float2* in, float2* out,
+                                const float2* tw, cudaStream_t st)
+{
+    cudaError_t e = cudaSuccess;
+    if (sign < 0) {
+#define ASFD_LTN(L) e = lines_L<L, -1>(in, out, lines, tw, st)
+        ASFD_FFT_SWITCH(n, ASFD_LTN)
+#undef ASFD_LTN
+    } else {
+#define ASFD_LTP(L) e = lines_L<L, 1>(in, out, lines, tw, st)
+        ASFD_FFT_SWITCH(n, ASFD_LTP)
+#undef ASFD_LTP
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "fft_lines_kernel launch");
+    return ASFD_OK;
+}
+
 asfd_status launch_fft_lines(int n, int lines, int sign, const float2* in, float2* out,
                              cudaStream_t st)
 {
