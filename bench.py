@@ -47,6 +47,8 @@ def parse_args():
     ap.add_argument("--cpu-seconds", type=float, default=10.0,
                     help="target CPU time of the oracle baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the width sweep, learned kernel, adjoint and batch lines")
     return ap.parse_args()
 
 
@@ -55,6 +57,23 @@ def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return world, rank, local
+
+
+def max_over_ranks(x: float, device, world: int) -> float:
+    """Maximum of a per-rank time over the process group (identity at N = 1)."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, world: int, seconds: float) -> float:
+    """Units processed by all ranks (each rank runs its own replica of the
+    workload) per second of the slowest rank."""
+    return world * units_per_rank / seconds
 
 
 def workload_config(name, width):
@@ -271,12 +290,8 @@ def run_ours(args):
 
     step_ms = [e[0].elapsed_time(e[3]) for e in evs]
     stage_ms = [[e[s].elapsed_time(e[s + 1]) for e in evs] for s in range(3)]
-    ms = statistics.mean(step_ms)
-    if world > 1:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * n_src / (ms * 1e-3)
+    ms = max_over_ranks(statistics.mean(step_ms), dev, world)
+    value = whole_job_rate(n_src, world, ms * 1e-3)
 
     # roofline of the dominant kernel (algorithmic bytes / event-timed duration)
     sb = stage_bytes(info, g)
@@ -304,12 +319,9 @@ def run_ours(args):
         t = time.perf_counter()
         plan.execute_host(hu1, hu2)
         e2e_t.append(time.perf_counter() - t)
-    e2e_s = statistics.mean(e2e_t)
-    if world > 1:
-        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e = {"value": world * n_src / e2e_s, "unit": UNIT, "h2d_bytes_per_step": hu1.numel() * 8,
+    e2e_s = max_over_ranks(statistics.mean(e2e_t), dev, world)
+    e2e = {"value": whole_job_rate(n_src, world, e2e_s), "unit": UNIT,
+           "h2d_bytes_per_step": hu1.numel() * 8,
            "d2h_bytes_per_step": hu2.numel() * 8}
 
     line = None
@@ -333,12 +345,117 @@ def run_ours(args):
                 "sample": f"{npts} seeded destination points of the {g['m2x']}x{g['m2y']} grid "
                           f"({el:.1f} s), each a direct FP64 sum over all {n_src} source samples; "
                           "scaled to source samples/s of the full transform"}
+            if not args.no_extras:
+                line.update(extra_measurements(args, g, u1, d1, pts, ref, flush, stream))
         print(json.dumps(line), flush=True)
     plan.close()
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
     return 0
+
+
+def time_device_ms(fn, steps, warmup, flush, stream):
+    """Mean CUDA-event time (ms) of fn() on `stream`, L2 flushed before each call
+    outside the timed interval."""
+    import torch
+    for _ in range(warmup):
+        flush.zero_()
+        fn()
+    torch.cuda.synchronize()
+    evs = []
+    for _ in range(steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        evs.append((e0, e1))
+    torch.cuda.synchronize()
+    return statistics.mean(a.elapsed_time(b) for a, b in evs)
+
+
+def extra_measurements(args, g, u1, d1, pts, ref_pts, flush, stream):
+    """Single-GPU context lines: the ES width sweep and the learned kernel at the
+    same workload (accuracy against the ES width-12 field and the oracle
+    points), the adjoint on the 4096^2 workload and the 24-surface batch."""
+    import numpy as np
+    import torch
+
+    from paper_1203_3583_gb300 import learned as L, workloads as W
+    from paper_1203_3583_gb300.fresnel import FresnelBatch, FresnelPlan
+
+    steps = max(5, min(args.steps, 20))
+    n_src = g["n1x"] * g["n1y"]
+    u1_d = torch.as_tensor(u1, device="cuda")
+    ref12 = L.reference_fields([(g, u1, d1)])[0]
+
+    def accuracy(out):
+        full = float(torch.linalg.vector_norm(out - ref12) / torch.linalg.vector_norm(ref12))
+        got = out.cpu().numpy()[pts[1], pts[0]].astype(np.complex128)
+        return full, float(np.linalg.norm(got - ref_pts) / np.linalg.norm(ref_pts))
+
+    res = {}
+    widths = {}
+    for w in (4, 5, 6, 7, 8):
+        with FresnelPlan(g, d1, kernel_width=w) as p:
+            out = torch.empty(p.shape2, dtype=torch.complex64, device="cuda")
+            ms = time_device_ms(lambda: p.execute(u1_d, out=out), steps, 3, flush, stream)
+            full, orc = accuracy(out)
+        widths[str(w)] = {"samples_per_s": n_src / (ms * 1e-3), "ms": ms,
+                          "rel_l2_vs_es12": full, "rel_l2_vs_oracle": orc}
+    res["es_widths"] = widths
+
+    t0 = time.perf_counter()
+    pairs = L.train_set()
+    model, losses = L.train_model(pairs)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    with FresnelPlan(g, d1, kind="learned") as p:
+        model.apply_to(p)
+        out = torch.empty(p.shape2, dtype=torch.complex64, device="cuda")
+        ms = time_device_ms(lambda: p.execute(u1_d, out=out), steps, 3, flush, stream)
+        full, orc = accuracy(out)
+    match = [w for w in sorted(widths, key=int) if widths[w]["rel_l2_vs_es12"] <= full]
+    res["learned"] = {
+        "kernel_width": 4, "samples_per_s": n_src / (ms * 1e-3), "ms": ms,
+        "rel_l2_vs_es12": full, "rel_l2_vs_oracle": orc,
+        "target_rel_l2": 1e-4, "meets_target": orc <= 1e-4,
+        "gain_vs_es4_error": widths["4"]["rel_l2_vs_es12"] / full,
+        "es_width_at_same_accuracy": int(match[0]) if match else None,
+        "speedup_vs_es_at_same_accuracy": (widths[match[0]]["ms"] / ms) if match else None,
+        "training": {"steps": len(losses), "seconds_incl_references": train_s,
+                     "pairs": len(pairs), "geometry": "smooth_random2048 at 512^2",
+                     "final_train_rel_l2": float(np.sqrt(losses[-1]))}}
+
+    ga, ua, da = W.make("tilt_bump4096")
+    with FresnelPlan(ga, da) as p:
+        ua_d = torch.as_tensor(ua, device="cuda")
+        u2a = p.execute(ua_d)
+        inten = (u2a.abs() ** 2)
+        target = torch.rand(inten.shape, generator=torch.Generator().manual_seed(5)).to("cuda") \
+            * 2 * inten.mean()
+        gu2 = (4 * (inten - target) * u2a).to(torch.complex64)
+        gu1 = torch.empty_like(ua_d)
+        gd1 = torch.empty(p.shape1, dtype=torch.float32, device="cuda")
+        ms = time_device_ms(lambda: p.adjoint(ua_d, gu2, gu1, gd1), steps, 3, flush, stream)
+    res["adjoint"] = {"workload": "tilt_bump4096 (4096^2 at 3.74 um, 532 nm, z0 0.15 m)",
+                      "samples_per_s": ga["n1x"] * ga["n1y"] / (ms * 1e-3), "ms": ms,
+                      "outputs": "dL/du1 (complex) and dL/dd1"}
+
+    items = W.make_batch()
+    with FresnelBatch([(gb, db) for gb, _, db in items]) as b:
+        u1s = [torch.as_tensor(ub, device="cuda") for _, ub, _ in items]
+        outs = [torch.empty((gb["m2y"], gb["m2x"]), dtype=torch.complex64, device="cuda")
+                for gb, _, _ in items]
+        ms = time_device_ms(lambda: b.execute(u1s, out=outs), steps, 3, flush, stream)
+        info = b.info()
+    res["batch"] = {"workload": "rgb_batch24 (24 surfaces, 256^2..2048^2, 450/532/633 nm)",
+                    "samples_per_s": info["source_samples"] / (ms * 1e-3), "ms": ms,
+                    "source_samples": info["source_samples"], "persistent_blocks": info["blocks"],
+                    "cuda_graph": bool(info["graph"])}
+    return res
 
 
 def main():
