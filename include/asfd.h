@@ -86,8 +86,10 @@ typedef struct {
     size_t device_bytes;     /* device memory owned by the plan                         */
     int spread_kind;         /* 0: conflict-free warp tiles (no atomics) -- used when   */
                              /*    the map n -> g is monotone with positive spacing and */
-                             /*    no footprint wraps; 1: shared-memory atomics         */
-    int stride_x, stride_y;  /* sample strides between lanes of one warp step (kind 0)  */
+                             /*    no footprint wraps; 1: shared-memory atomics;        */
+                             /*    2: conflict-free warp tiles with a sliding register  */
+                             /*    window per lane (ES widths up to 8)                  */
+    int stride_x, stride_y;  /* sample strides between lanes of one warp step (0, 2)    */
 } asfd_plan_info;
 
 /*

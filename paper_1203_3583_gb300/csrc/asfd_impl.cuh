@@ -19,6 +19,7 @@ constexpr int kTileY = 64;
 constexpr int kSrcTile = 16;  // source tiles are kSrcTile x kSrcTile samples
 constexpr int kColTileY = 32; // rows of a tile of the conflict-free spreading kernel
 constexpr int kMaxRingWidth = 14;  // widest kernel of the conflict-free spreading path (no spills)
+constexpr int kMaxWindowWidth = 8;  // widest kernel of the register-window spreading path
 
 // Learned spreading kernel: width kLearnW, per-source-tile polynomial of
 // degree kLearnDeg per tap and axis in t = 2 dx - 1, an MLP of kLearnFeat
@@ -110,8 +111,9 @@ struct asfd_plan_s {
     double2* row_range = nullptr;   // per source row:    [min, max] of the y storage coordinate
     float2* step_min = nullptr;     // per block of min_step_kernel: min spacing along x and y
     bool colored = false;
-    int sx_min = 0, h_min = 0;
-    double min_step_x = 0.0, min_step_y = 0.0, row_spread_y = 0.0;
+    bool windowed = false;          // register-window kernel applies (w <= kMaxWindowWidth)
+    int sx_min = 0, h_min = 0, sxw_min = 0;
+    double min_step_x = 0.0, min_step_y = 0.0, row_spread_y = 0.0, col_spread_x = 0.0;
     long long tile_pairs = 0;
     size_t tile_src_cap = 0;
 

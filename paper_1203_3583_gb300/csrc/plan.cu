@@ -583,6 +583,10 @@ asfd_status plan_build_colored(asfd_plan_s* P, bool wraps, cudaStream_t st)
         msy = std::min(msy, (double)sm[2 * b + 1]);
     }
     for (int ny = 0; ny < p.n1y; ++ny) spread_y = std::max(spread_y, rr[2 * ny + 1] - rr[2 * ny]);
+    double spread_x = 0.0;
+    for (int nx = 0; nx < p.n1x; ++nx) spread_x = std::max(spread_x, cr[2 * nx + 1] - cr[2 * nx]);
+    P->col_spread_x = spread_x;
+    P->windowed = false;
     if (p.n1x < 2) msx = 1e30;
     if (p.n1y < 2) msy = 1e30;
     P->min_step_x = msx;
@@ -642,6 +646,12 @@ asfd_status plan_build_colored(asfd_plan_s* P, bool wraps, cudaStream_t st)
     P->sx_min = (int)sxd;
     P->h_min = (int)hd;
     P->colored = true;
+    // the register-window kernel also needs columns w apart across rows
+    const double sxw = std::ceil((P->w + spread_x + margin) / msx);
+    if (P->w <= kMaxWindowWidth && sxw <= 64.0) {
+        P->sxw_min = (int)sxw;
+        P->windowed = true;
+    }
     return ASFD_OK;
 }
 

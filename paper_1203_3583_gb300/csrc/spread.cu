@@ -32,6 +32,10 @@
 //    apart, row groups take rows at least H apart, where Sx and H follow from
 //    the minimum spacing of the samples on the fine grid (the map n -> g is
 //    monotone for a non-folding surface).  A __syncwarp separates steps.
+//  * spread_es_window_kernel (widths up to kMaxWindowWidth, same lanes):
+//    each lane walks its samples down a source column and keeps their taps
+//    in a sliding W x W register window, so that shared memory sees about
+//    one row of W updates per sample instead of W rows.
 //  * spread_es_atomic_kernel (fallback for folding or wrapping maps):
 //    256 threads, one sample per thread, shared-memory atomics.
 #include "spread.cuh"
@@ -49,8 +53,15 @@ __global__ void __launch_bounds__(256) spread_es_atomic_kernel(SpreadArgs a)
 }
 
 template <int W>
-cudaError_t launch_w(const SpreadArgs& a, int tiles, bool colored, cudaStream_t st)
+cudaError_t launch_w(const SpreadArgs& a, int tiles, bool colored, bool windowed, cudaStream_t st)
 {
+    if constexpr (W <= kMaxWindowWidth) {
+        if (windowed) {
+            spread_es_window_kernel<W, kTileX, kColTileY, false>
+                <<<tiles * (kTileY / kColTileY), 32, 0, st>>>(a);
+            return cudaGetLastError();
+        }
+    }
     // widths up to kMaxRingWidth compile without register spills
     if constexpr (W <= kMaxRingWidth) {
         if (colored) {
@@ -98,6 +109,7 @@ SpreadArgs make_spread_args(const asfd_plan_s* P, const float2* u1)
     a.band_ntx = P->band_tx1 - P->band_tx0;
     a.sx_min = P->sx_min;
     a.h_min = P->h_min;
+    a.sxw_min = P->sxw_min;
     a.half_w = 0.5f * (float)P->w;
     a.beta_log2e = (float)(P->beta * 1.4426950408889634074);
     a.two_over_w = (float)(2.0 / P->w);
@@ -111,6 +123,7 @@ asfd_status launch_spread(asfd_plan_s* P, const float2* u1, cudaStream_t st)
     const int tiles = (P->band_tx1 - P->band_tx0) * (P->band_ty1 - P->band_ty0);
     if (tiles <= 0) return ASFD_OK;
     const bool colored = P->colored;
+    const bool windowed = P->colored && P->windowed;
     cudaError_t e;
     if (P->learned) {
         e = launch_table(a, tiles, colored, st);
@@ -118,21 +131,21 @@ asfd_status launch_spread(asfd_plan_s* P, const float2* u1, cudaStream_t st)
         return ASFD_OK;
     }
     switch (P->w) {
-        case 2: e = launch_w<2>(a, tiles, colored, st); break;
-        case 3: e = launch_w<3>(a, tiles, colored, st); break;
-        case 4: e = launch_w<4>(a, tiles, colored, st); break;
-        case 5: e = launch_w<5>(a, tiles, colored, st); break;
-        case 6: e = launch_w<6>(a, tiles, colored, st); break;
-        case 7: e = launch_w<7>(a, tiles, colored, st); break;
-        case 8: e = launch_w<8>(a, tiles, colored, st); break;
-        case 9: e = launch_w<9>(a, tiles, colored, st); break;
-        case 10: e = launch_w<10>(a, tiles, colored, st); break;
-        case 11: e = launch_w<11>(a, tiles, colored, st); break;
-        case 12: e = launch_w<12>(a, tiles, colored, st); break;
-        case 13: e = launch_w<13>(a, tiles, colored, st); break;
-        case 14: e = launch_w<14>(a, tiles, colored, st); break;
-        case 15: e = launch_w<15>(a, tiles, colored, st); break;
-        case 16: e = launch_w<16>(a, tiles, colored, st); break;
+        case 2: e = launch_w<2>(a, tiles, colored, windowed, st); break;
+        case 3: e = launch_w<3>(a, tiles, colored, windowed, st); break;
+        case 4: e = launch_w<4>(a, tiles, colored, windowed, st); break;
+        case 5: e = launch_w<5>(a, tiles, colored, windowed, st); break;
+        case 6: e = launch_w<6>(a, tiles, colored, windowed, st); break;
+        case 7: e = launch_w<7>(a, tiles, colored, windowed, st); break;
+        case 8: e = launch_w<8>(a, tiles, colored, windowed, st); break;
+        case 9: e = launch_w<9>(a, tiles, colored, windowed, st); break;
+        case 10: e = launch_w<10>(a, tiles, colored, windowed, st); break;
+        case 11: e = launch_w<11>(a, tiles, colored, windowed, st); break;
+        case 12: e = launch_w<12>(a, tiles, colored, windowed, st); break;
+        case 13: e = launch_w<13>(a, tiles, colored, windowed, st); break;
+        case 14: e = launch_w<14>(a, tiles, colored, windowed, st); break;
+        case 15: e = launch_w<15>(a, tiles, colored, windowed, st); break;
+        case 16: e = launch_w<16>(a, tiles, colored, windowed, st); break;
         default: return fail(ASFD_ERR_UNSUPPORTED, "kernel width outside 2..16");
     }
     if (e != cudaSuccess) return cuda_fail(e, "spread kernel launch");
