@@ -19,7 +19,7 @@ constexpr int kTileY = 64;
 constexpr int kSrcTile = 16;  // source tiles are kSrcTile x kSrcTile samples
 constexpr int kColTileY = 32; // rows of a tile of the conflict-free spreading kernel
 constexpr int kMaxRingWidth = 14;  // widest kernel of the conflict-free spreading path (no spills)
-constexpr int kMaxWindowWidth = 8;  // widest kernel of the register-window spreading path
+constexpr int kMaxWindowWidth = 7;  // widest kernel of the register-window spreading path
 
 // Learned spreading kernel: width kLearnW, per-source-tile polynomial of
 // degree kLearnDeg per tap and axis in t = 2 dx - 1, an MLP of kLearnFeat

@@ -56,6 +56,27 @@ __device__ __forceinline__ float2 fma2(float2 v, float w, float2 acc)
     return *reinterpret_cast<float2*>(&r);
 }
 
+// v * w and a * b + c on complex pairs / FP32 pairs (packed FP32x2)
+__device__ __forceinline__ float2 mul2(float2 v, float w)
+{
+    unsigned long long r;
+    const unsigned long long vv = *reinterpret_cast<const unsigned long long*>(&v);
+    const float2 ww = make_float2(w, w);
+    const unsigned long long wb = *reinterpret_cast<const unsigned long long*>(&ww);
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(vv), "l"(wb));
+    return *reinterpret_cast<float2*>(&r);
+}
+
+__device__ __forceinline__ float2 fma2v(float2 a, float2 b, float2 c)
+{
+    unsigned long long r;
+    const unsigned long long aa = *reinterpret_cast<const unsigned long long*>(&a);
+    const unsigned long long bb = *reinterpret_cast<const unsigned long long*>(&b);
+    const unsigned long long cc = *reinterpret_cast<const unsigned long long*>(&c);
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(aa), "l"(bb), "l"(cc));
+    return *reinterpret_cast<float2*>(&r);
+}
+
 // Per-sample inputs, loaded one sample ahead of use.
 struct Raw {
     float q;
@@ -94,16 +115,22 @@ __device__ __forceinline__ float es_weight_fast(float z, float two_over_w, float
 // c = u1 E_x E_y exp(i pi (a_x + a_y) q); the correction phase is reduced
 // modulo 2 half-turns exactly in FP32, then evaluated with the MUFU sine and
 // cosine (absolute error ~4e-7 on [-pi, pi]).
-__device__ __forceinline__ float2 sample_value_fast(const Raw& r)
+__device__ __forceinline__ float2 sample_value_fast(float2 u, const AxisEntry& ex,
+                                                    const AxisEntry& ey, float q)
 {
-    const float ph = (r.ex.a + r.ey.a) * r.q;
+    const float ph = (ex.a + ey.a) * q;
     const float red = ph - 2.0f * rintf(0.5f * ph);
     float sn, cs;
     __sincosf(3.14159265358979f * red, &sn, &cs);
-    const float2 exy = make_float2(r.ex.e.x * r.ey.e.x - r.ex.e.y * r.ey.e.y,
-                                   r.ex.e.x * r.ey.e.y + r.ex.e.y * r.ey.e.x);
-    const float2 t1 = make_float2(r.u.x * exy.x - r.u.y * exy.y, r.u.x * exy.y + r.u.y * exy.x);
+    const float2 exy = make_float2(ex.e.x * ey.e.x - ex.e.y * ey.e.y,
+                                   ex.e.x * ey.e.y + ex.e.y * ey.e.x);
+    const float2 t1 = make_float2(u.x * exy.x - u.y * exy.y, u.x * exy.y + u.y * exy.x);
     return make_float2(t1.x * cs - t1.y * sn, t1.x * sn + t1.y * cs);
+}
+
+__device__ __forceinline__ float2 sample_value_fast(const Raw& r)
+{
+    return sample_value_fast(r.u, r.ex, r.ey, r.q);
 }
 
 }  // namespace asfd

@@ -159,27 +159,75 @@ __global__ void __launch_bounds__(32) spread_es_colored_kernel(SpreadArgs a)
     colored_tile<W, TX, TY, TAB>(a, blockIdx.x, tile, threadIdx.x);
 }
 
-// Register-window spreading: the lanes of colored_tile, but each lane walks
-// its samples down source columns (runs of h consecutive rows at a fixed
-// column) and accumulates their taps in a W x W window of registers that
-// slides down the fine grid with the samples.  A row of the window is added
-// to the shared-memory tile only when the next sample's first tap row has
-// passed it, so a sample costs about one row of W read-modify-writes instead
-// of W rows; the window is flushed whole when the first tap column changes
-// and at the end of every run, in a step of its own.
+// Register-window spreading.  Lanes are those of colored_tile (4 row groups x
+// 8 column groups) and, as there, every lane takes one sample per warp step,
+// but a lane walks its samples down a source column (a run of h consecutive
+// rows at a fixed column) and accumulates their taps in a window of W rows x
+// (W + 1) columns of registers that slides down the fine grid with the
+// samples.  When the next sample's first tap row is d = 1 or 2 rows lower,
+// the d top rows are added to the shared-memory tile and the sample's taps
+// are accumulated into the remaining rows moved up by d in the same FMAs
+// (row b takes row b + d plus the new taps), so sliding costs no register
+// moves; a larger jump, a sample that misses the tile, and the end of a run
+// flush the whole window.  The spare column absorbs a first tap column that
+// changes by one within the run (the window starts at the smaller of the
+// run's first and last sample's first tap column).  A sample is never added
+// to the tile directly, so each cell of the tile receives about one
+// read-modify-write per sample row instead of one per tap row.
 //
 // Disjointness of the shared-memory updates of one step: a lane only writes
 // rows of the window of its previous step's sample, [R0, R0 + W) with R0 that
 // sample's first tap row (a window whose lane found no sample in this step is
-// flushed in this step).  Lanes of one row group hold columns at least
+// flushed in this step), and only columns covered by its own samples' taps.
+// Lanes of one row group hold columns at least
 // sx * min_step_x - column_spread_x >= w apart (column_spread_x bounds the
 // variation of the x coordinate down a column, since the two lanes' windows
 // may come from different rows of their runs); lanes of different row groups
 // are h rows apart in the same step, h * min_step_y - row_spread_y >= w.
+constexpr int kWindowSpare = 1;  // spare window columns (first tap column drift in a run)
+
+template <int WX, int TX, int TY>
+__device__ __forceinline__ void window_flush(float2* tile, int row, int cx, unsigned cmask,
+                                             const float2 (&r)[WX])
+{
+    constexpr int LD = ColoredTile<TX, TY>::LD;
+    if ((unsigned)row < (unsigned)TY) {
+        float2* p = tile + row * LD;
+        float2 v[WX];
+#pragma unroll
+        for (int i = 0; i < WX; ++i)
+            v[i] = ((cmask >> i) & 1u) ? p[cx + i] : make_float2(0.f, 0.f);
+#pragma unroll
+        for (int i = 0; i < WX; ++i)
+            if ((cmask >> i) & 1u) p[cx + i] = make_float2(v[i].x + r[i].x, v[i].y + r[i].y);
+    }
+}
+
+// ES weights of two taps at once (packed FP32x2 arithmetic; the square root
+// and exponential on the MUFU unit as in es_weight_fast).
+__device__ __forceinline__ float2 es_weight2_fast(float2 z, float neg_c2, float beta_log2e)
+{
+    // r = 1 - (2z/w)^2 = fma(z * neg_c2, z, 1)
+    const float2 t = mul2(z, neg_c2);
+    float2 r = fma2v(t, z, make_float2(1.f, 1.f));
+    r.x = fmaxf(r.x, 1e-30f);
+    r.y = fmaxf(r.y, 1e-30f);
+    float2 rs, e;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(rs.x) : "f"(r.x));
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(rs.y) : "f"(r.y));
+    const float2 s = fma2v(r, rs, make_float2(-1.f, -1.f));
+    const float2 arg = mul2(s, beta_log2e);
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e.x) : "f"(arg.x));
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e.y) : "f"(arg.y));
+    return e;
+}
+
 template <int W, int TX, int TY, bool TAB>
 __device__ __forceinline__ void window_tile(const SpreadArgs& a, int t, float2* tile, int lane)
 {
+    static_assert(!TAB, "the register-window kernel evaluates the ES kernel");
     constexpr int LD = ColoredTile<TX, TY>::LD;
+    constexpr int WX = W + kWindowSpare;
     const int ox = (a.band_tx0 + t % a.band_ntx) * TX;
     const int oy = a.band_ty0 * kTileY + (t / a.band_ntx) * TY;
 
@@ -193,94 +241,169 @@ __device__ __forceinline__ void window_tile(const SpreadArgs& a, int t, float2* 
         const int sx = max(a.sxw_min, (rw + 7) / 8);
         const int h = max(a.h_min, (rh + 3) / 4);
         const int nx0 = rc.x + lc * sx, ny0 = rc.z + lr * h;
+        const int nyl = min(ny0 + h, rc.w) - 1;  // last source row of this lane's runs
         const int nsamp = sx * h;
+        const float neg_c2 = -a.two_over_w * a.two_over_w;
 
-        float2 acc[W][W];
+        float2 acc[W][WX];
 #pragma unroll
         for (int b = 0; b < W; ++b)
 #pragma unroll
-            for (int i = 0; i < W; ++i) acc[b][i] = make_float2(0.f, 0.f);
-        int X0 = 0, R0 = 0;
+            for (int i = 0; i < WX; ++i) acc[b][i] = make_float2(0.f, 0.f);
+        int X0 = 0, R0 = 0, maxoff = 0;
+        unsigned cmask = 0;
         bool live = false;
 
-        // add window row b to tile row `row` (tile-relative) at columns X0..
-        auto flush_row = [&](int b, int row) {
-            if ((unsigned)row < (unsigned)TY) {
-                const int cx = X0 - ox;
-                float2* p = tile + row * LD + cx;
-                float2 v[W];
-#pragma unroll
-                for (int i = 0; i < W; ++i)
-                    v[i] = ((unsigned)(cx + i) < (unsigned)TX) ? p[i] : make_float2(0.f, 0.f);
-#pragma unroll
-                for (int i = 0; i < W; ++i)
-                    if ((unsigned)(cx + i) < (unsigned)TX)
-                        p[i] = make_float2(v[i].x + acc[b][i].x, v[i].y + acc[b][i].y);
-            }
-        };
+        // (a window that is not live holds stale values: the first sample
+        // of the next window overwrites every slot)
         auto flush_all = [&]() {
 #pragma unroll
-            for (int b = 0; b < W; ++b) {
-                flush_row(b, R0 - oy + b);
+            for (int b = 0; b < W; ++b)
+                window_flush<WX, TX, TY>(tile, R0 - oy + b, X0 - ox, cmask, acc[b]);
+        };
+        // window columns X0 .. X0 + W - 1 + maxoff (within the tile)
+        auto set_columns = [&](int x0, int mo) {
+            X0 = x0;
+            maxoff = mo;
+            cmask = 0;
 #pragma unroll
-                for (int i = 0; i < W; ++i) acc[b][i] = make_float2(0.f, 0.f);
-            }
+            for (int i = 0; i < WX; ++i)
+                if (i < W + mo && (unsigned)(x0 - ox + i) < (unsigned)TX) cmask |= 1u << i;
         };
 
-        int o = 0, j = 0;
-        bool v = (nx0 < rc.y) && (ny0 < rc.w);
-        Raw cur;
-        if (v) cur = load_raw(a, nx0, ny0);
-        for (int s = 0; s < nsamp; ++s) {
-            int o2 = o, j2 = j + 1;
-            if (j2 == h) {
-                j2 = 0;
-                ++o2;
+        // u1 and q of the samples two steps ahead are loaded in flight; the
+        // column's table entries are fixed for a run, the row's are read at use
+        int o = 0, j = 0;    // step s: run o, row j
+        int oc = 0, jc = 0;  // step s + 2
+        auto next_slot = [&](int& oo, int& jj) {
+            if (++jj == h) {
+                jj = 0;
+                ++oo;
             }
-            const bool v2 = (s + 1 < nsamp) && (nx0 + o2 < rc.y) && (ny0 + j2 < rc.w);
-            Raw nxt;
-            if (v2) nxt = load_raw(a, nx0 + o2, ny0 + j2);
+        };
+        auto slot_ok = [&](int oo, int jj) { return (nx0 + oo < rc.y) && (ny0 + jj <= nyl); };
+        next_slot(oc, jc);
+        next_slot(oc, jc);
+        float qa = 0.f, qb = 0.f;
+        float2 ua = make_float2(0.f, 0.f), ub = make_float2(0.f, 0.f);
+        if (slot_ok(0, 0)) {
+            qa = __ldg(&a.q[(size_t)ny0 * a.n1x + nx0]);
+            ua = __ldg(&a.u1[(size_t)ny0 * a.n1x + nx0]);
+        }
+        if (nsamp > 1) {
+            int o1 = 0, j1 = 0;
+            next_slot(o1, j1);
+            if (slot_ok(o1, j1)) {
+                const size_t n = (size_t)(ny0 + j1) * a.n1x + nx0 + o1;
+                qb = __ldg(&a.q[n]);
+                ub = __ldg(&a.u1[n]);
+            }
+        }
+        AxisEntry ex{};
+        AxisPos px{};
+        for (int s = 0; s < nsamp; ++s) {
+            float qc = 0.f;
+            float2 uc = make_float2(0.f, 0.f);
+            if (s + 2 < nsamp && slot_ok(oc, jc)) {
+                const size_t n = (size_t)(ny0 + jc) * a.n1x + nx0 + oc;
+                qc = __ldg(&a.q[n]);
+                uc = __ldg(&a.u1[n]);
+            }
+            const bool v = slot_ok(o, j);
+            const int nx = nx0 + o, ny = ny0 + j;
             int l0x = 0, l0y = 0;
             float dx = 0.f, dy = 0.f;
             bool hit = false;
+            AxisEntry ey{};
             if (v) {
-                sample_pos(cur.ex, cur.ey, cur.px, cur.py, cur.q, a.half_w, l0x, l0y, dx, dy);
-                const int cx = l0x - ox, cy = l0y - oy;
-                hit = cx > -W && cx < TX && cy > -W && cy < TY;
+                if (j == 0) {
+                    ex = a.ax[nx];
+                    px = a.px[nx];
+                }
+                ey = a.ay[ny];
+                const AxisPos py = a.py[ny];
+                sample_pos(ex, ey, px, py, qa, a.half_w, l0x, l0y, dx, dy);
+                hit = (l0x - ox) > -W && (l0x - ox) < TX && (l0y - oy) > -W && (l0y - oy) < TY;
+                if (j == 0) {
+                    // window columns of the run: first tap columns of its first
+                    // and last samples
+                    const float ql = __ldg(&a.q[(size_t)nyl * a.n1x + nx]);
+                    int lx, ly;
+                    float fx, fy;
+                    sample_pos(ex, a.ay[nyl], px, a.py[nyl], ql, a.half_w, lx, ly, fx, fy);
+                    if (kWindowSpare > 0) set_columns(min(l0x, lx), lx != l0x ? 1 : 0);
+                    else set_columns(l0x, 0);
+                }
             }
-            // A window is written only in the step right after its last
-            // sample: a lane whose samples have left the tile flushes now, not
-            // at the end of the run, when the lane of the next row group may
-            // have come down next to it.
-            if (live && (!hit || l0x != X0 || l0y < R0 || l0y - R0 >= W)) {
+            const int off = l0x - X0;
+            const int d = l0y - R0;
+            if (live && (!hit || off < 0 || off > maxoff || d < 0 || d > 2)) {
                 flush_all();
                 live = false;
             }
             if (hit) {
-                const float2 c = sample_value_fast(cur);
-                float wx[W], wy[W];
-                tap_weights<W, TAB>(a, nx0 + o, ny0 + j, dx, dy, wx, wy);
-                if (!live) {
-                    X0 = l0x;
+                const bool fresh = !live;
+                if (fresh) {
+                    if (off < 0 || off > maxoff) set_columns(l0x, 0);
                     R0 = l0y;
                     live = true;
                 }
-                while (R0 < l0y) {  // slide the window down one row
-                    flush_row(0, R0 - oy);
-#pragma unroll
-                    for (int b = 0; b + 1 < W; ++b)
-#pragma unroll
-                        for (int i = 0; i < W; ++i) acc[b][i] = acc[b + 1][i];
-#pragma unroll
-                    for (int i = 0; i < W; ++i) acc[W - 1][i] = make_float2(0.f, 0.f);
-                    ++R0;
-                }
+                const int offn = l0x - X0;
+                const int dn = l0y - R0;
+                const float2 c = sample_value_fast(ua, ex, ey, qa);
+                float wy[W], wxe[WX];
+                const float by = dy - a.half_w;
+                const float bx = dx - a.half_w - (float)offn;
 #pragma unroll
                 for (int b = 0; b < W; ++b) {
-                    const float2 cb = make_float2(c.x * wy[b], c.y * wy[b]);
-#pragma unroll
-                    for (int i = 0; i < W; ++i) acc[b][i] = fma2(cb, wx[i], acc[b][i]);
+                    const float2 e = es_weight2_fast(make_float2(by + (float)b, bx + (float)b),
+                                                     neg_c2, a.beta_log2e);
+                    wy[b] = e.x;
+                    wxe[b] = e.y;
                 }
+                if constexpr (WX > W) {
+                    wxe[W] = es_weight_fast(bx + (float)W, a.two_over_w, a.beta_log2e);
+                    // tap column i of the sample sits in window column i + offn
+                    if (offn == 1) wxe[0] = 0.f;
+                    else wxe[W] = 0.f;
+                }
+                if (fresh) {
+#pragma unroll
+                    for (int b = 0; b < W; ++b) {
+                        const float2 cb = mul2(c, wy[b]);
+#pragma unroll
+                        for (int i = 0; i < WX; ++i) acc[b][i] = mul2(cb, wxe[i]);
+                    }
+                } else if (dn == 0) {
+#pragma unroll
+                    for (int b = 0; b < W; ++b) {
+                        const float2 cb = mul2(c, wy[b]);
+#pragma unroll
+                        for (int i = 0; i < WX; ++i) acc[b][i] = fma2(cb, wxe[i], acc[b][i]);
+                    }
+                } else if (dn == 1) {
+                    window_flush<WX, TX, TY>(tile, R0 - oy, X0 - ox, cmask, acc[0]);
+#pragma unroll
+                    for (int b = 0; b < W; ++b) {
+                        const float2 cb = mul2(c, wy[b]);
+#pragma unroll
+                        for (int i = 0; i < WX; ++i)
+                            acc[b][i] = (b + 1 < W) ? fma2(cb, wxe[i], acc[b + 1][i])
+                                                    : mul2(cb, wxe[i]);
+                    }
+                } else {
+                    window_flush<WX, TX, TY>(tile, R0 - oy, X0 - ox, cmask, acc[0]);
+                    window_flush<WX, TX, TY>(tile, R0 + 1 - oy, X0 - ox, cmask, acc[1]);
+#pragma unroll
+                    for (int b = 0; b < W; ++b) {
+                        const float2 cb = mul2(c, wy[b]);
+#pragma unroll
+                        for (int i = 0; i < WX; ++i)
+                            acc[b][i] = (b + 2 < W) ? fma2(cb, wxe[i], acc[b + 2][i])
+                                                    : mul2(cb, wxe[i]);
+                    }
+                }
+                R0 = l0y;
             }
             __syncwarp();
             if (j == h - 1) {  // end of run: flush in a step of its own
@@ -288,10 +411,12 @@ __device__ __forceinline__ void window_tile(const SpreadArgs& a, int t, float2* 
                 live = false;
                 __syncwarp();
             }
-            cur = nxt;
-            v = v2;
-            o = o2;
-            j = j2;
+            qa = qb;
+            ua = ub;
+            qb = qc;
+            ub = uc;
+            next_slot(o, j);
+            next_slot(oc, jc);
         }
     }
     __syncwarp();
