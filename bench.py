@@ -166,7 +166,13 @@ def stage_bytes(info, g):
     return [spread, rows, cols]
 
 
-STAGE_KERNELS = ["spread_es_kernel", "fft_rows_kernel", "fft_cols_kernel"]
+STAGE_KERNELS = ["spread", "fft_rows_kernel", "fft_cols_kernel"]
+SPREAD_KERNEL = {0: "spread_es_colored_kernel", 1: "spread_es_atomic_kernel",
+                 2: "spread_es_window_kernel", 3: "spread_es_dense_kernel"}
+# bytes per source sample of the whole forward step in the unpruned model:
+# u1 + d1 (12) + fine-grid write (4 M^2 8 / N^2 = 32) + row read (32) + row write
+# (16) + column read (16) + u2 write (8), sigma = 2 and N = M
+STEP_BYTES_PER_SAMPLE = 116
 
 
 def oracle_sample(g, u1, d1, seconds, seed=7):
@@ -299,13 +305,21 @@ def run_ours(args):
     dom = int(np.argmax(mean_stage))
     peak, peak_src = measured_peaks()
     achieved = sb[dom] / (mean_stage[dom] * 1e-3) / 1e9
-    roofline = {"bound": "hbm", "kernel": f"{STAGE_KERNELS[dom]}<{args.width if dom == 0 else ''}>"
-                .replace("<>", ""), "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": None,
+    names = [f"{SPREAD_KERNEL[info['spread_kind']]}<{args.width}>"] + STAGE_KERNELS[1:]
+    roofline = {"bound": "hbm", "kernel": names[dom], "achieved": achieved, "peak": peak,
+                "unit": "GB/s", "frac": achieved / peak, "traffic": None,
                 "algorithmic_bytes_per_launch": sb[dom], "peak_source": peak_src,
-                "stage_ms": {k: v for k, v in zip(STAGE_KERNELS, mean_stage)},
+                "stage_ms": {k: v for k, v in zip(names, mean_stage)},
                 "stage_frac": {k: b / (t * 1e-3) / 1e9 / peak
-                               for k, b, t in zip(STAGE_KERNELS, sb, mean_stage)}}
+                               for k, b, t in zip(names, sb, mean_stage)}}
+    # the whole step against the unpruned spread+FFT memory model
+    step_bytes = STEP_BYTES_PER_SAMPLE * n_src
+    step_roofline = {"bound": "hbm", "bytes_per_sample": STEP_BYTES_PER_SAMPLE,
+                     "bytes_per_step": step_bytes,
+                     "achieved": step_bytes / (statistics.mean(step_ms) * 1e-3) / 1e9,
+                     "peak": peak, "unit": "GB/s",
+                     "frac": step_bytes / (statistics.mean(step_ms) * 1e-3) / 1e9 / peak,
+                     "pruned_bytes_per_step": sum(sb)}
 
     # end to end through the C ABI with pinned host buffers
     hu1 = torch.as_tensor(u1).pin_memory()
@@ -330,7 +344,8 @@ def run_ours(args):
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                 "data": "synthetic", "config": workload_config(args.workload, args.width),
-                "roofline": roofline, "e2e": e2e, "clocks": clk,
+                "roofline": roofline, "step_roofline": step_roofline, "e2e": e2e, "clocks": clk,
+                "spread_kind": info["spread_kind"],
                 "gpu_launches": 3 * args.steps, "plan_ms": plan_ms,
                 "wall_s_timed_region": wall,
                 "plan": {k: info[k] for k in ("nfx", "nfy", "band_x0", "band_x1", "band_y0",
@@ -397,6 +412,15 @@ def extra_measurements(args, g, u1, d1, pts, ref_pts, flush, stream):
         return full, float(np.linalg.norm(got - ref_pts) / np.linalg.norm(ref_pts))
 
     res = {}
+    # the atomic-free (bit-reproducible) spreading path on the same workload
+    with FresnelPlan(g, d1, kernel_width=args.width, deterministic=True) as p:
+        out = torch.empty(p.shape2, dtype=torch.complex64, device="cuda")
+        ms = time_device_ms(lambda: p.execute(u1_d, out=out), steps, 3, flush, stream)
+        sp = time_device_ms(lambda: p.execute_stage(0, u1=u1_d), steps, 3, flush, stream)
+        full, orc = accuracy(out)
+        kind = p.info()["spread_kind"]
+    res["deterministic"] = {"spread_kernel": SPREAD_KERNEL[kind], "samples_per_s": n_src / (ms * 1e-3),
+                            "ms": ms, "spread_ms": sp, "rel_l2_vs_oracle": orc}
     widths = {}
     for w in (4, 5, 6, 7, 8):
         with FresnelPlan(g, d1, kernel_width=w) as p:

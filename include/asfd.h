@@ -69,6 +69,12 @@ typedef struct {
     int kernel_width;    /* spreading kernel width w in fine-grid cells, 2..16          */
     double es_beta;      /* ES shape parameter; 0 selects 2.30*w at sigma = 2           */
     asfd_kernel_kind kind;
+    int deterministic;   /* 0 (fastest): for monotone maps and ES widths up to 7 the    */
+                         /*   spread accumulates register windows into the fine grid   */
+                         /*   with float atomic adds, so the last bits of a result may  */
+                         /*   differ from run to run; 1: conflict-free shared-memory    */
+                         /*   tiles without atomics where the map allows them (results */
+                         /*   bit-identical run to run), shared-memory atomics else     */
 } asfd_params;
 
 typedef struct asfd_plan_s* asfd_plan;
@@ -88,7 +94,9 @@ typedef struct {
                              /*    the map n -> g is monotone with positive spacing and */
                              /*    no footprint wraps; 1: shared-memory atomics;        */
                              /*    2: conflict-free warp tiles with a sliding register  */
-                             /*    window per lane (ES widths up to 8)                  */
+                             /*    window per lane (ES widths up to 7); 3: dense maps   */
+                             /*    (many samples per cell): register windows flushed    */
+                             /*    to the fine grid with atomic adds (widths up to 7)   */
     int stride_x, stride_y;  /* sample strides between lanes of one warp step (0, 2)    */
 } asfd_plan_info;
 

@@ -48,6 +48,7 @@ class Params(ctypes.Structure):
         ("kernel_width", ctypes.c_int),
         ("es_beta", ctypes.c_double),
         ("kind", ctypes.c_int),
+        ("deterministic", ctypes.c_int),
     ]
 
 
@@ -215,12 +216,12 @@ def _dev_ptr(t: torch.Tensor, dtype, shape, name):
 
 
 def make_params(g: dict, sigma: float = 2.0, kernel_width: int = 7, es_beta: float = 0.0,
-                kind: int = ASFD_KERNEL_ES) -> Params:
+                kind: int = ASFD_KERNEL_ES, deterministic: bool = False) -> Params:
     """asfd_params from a geometry dict (keys of workloads.geometry)."""
     return Params(int(g["n1x"]), int(g["n1y"]), float(g["p1x"]), float(g["p1y"]),
                   int(g["m2x"]), int(g["m2y"]), float(g["p2x"]), float(g["p2y"]),
                   float(g["lam"]), float(g["z0"]), float(sigma), int(kernel_width),
-                  float(es_beta), int(kind))
+                  float(es_beta), int(kind), int(bool(deterministic)))
 
 
 def asfd_plan_create(params: Params, d1: torch.Tensor, stream=None) -> ctypes.c_void_p:

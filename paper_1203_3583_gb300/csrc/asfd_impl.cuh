@@ -112,6 +112,8 @@ struct asfd_plan_s {
     float2* step_min = nullptr;     // per block of min_step_kernel: min spacing along x and y
     bool colored = false;
     bool windowed = false;          // register-window kernel applies (w <= kMaxWindowWidth)
+    bool dense = false;             // dense map: register windows flushed with global atomics
+    int dense_rows = 0, dense_items = 0;
     int sx_min = 0, h_min = 0, sxw_min = 0;
     double min_step_x = 0.0, min_step_y = 0.0, row_spread_y = 0.0, col_spread_x = 0.0;
     long long tile_pairs = 0;

@@ -4,8 +4,12 @@
 //
 // Each surface has its own plan (tables, binning, work buffers).  The kernel
 // runs stage-major over the whole batch:
-//   stage 0  every warp takes (surface, fine-grid tile) items of the
-//            conflict-free spread (8 warps per block, one tile each);
+//   stage Z  (when some surface uses the dense spread) clear the bands of
+//            those surfaces, then a grid barrier;
+//   stage 0  every block takes the shared-memory-atomic tiles of surfaces
+//            that need them, then every warp takes (surface, item) items: a
+//            conflict-free fine-grid tile, or a dense item (32 source columns
+//            whose register windows are flushed with atomic adds);
 //   grid barrier (cooperative groups: all blocks are co-resident, as the
 //            cooperative launch guarantees, so the barrier cannot deadlock);
 //   stage 1  every block takes (surface, row group) items of the row FFT;
@@ -43,7 +47,9 @@ struct BatchSurf {
     RowArgs ra;
     ColArgs ca;
     int nfx, nfy;
+    int windowed;      // conflict-free tiles use the register-window form
     int tile0, ntile;  // first item and count of conflict-free (warp) spread tiles
+    int dense0, ndense;  // first item and count of dense (global-atomic) warp items
     int atile0, natile;  // first item and count of atomic (block) spread tiles
     int row0, nrow;    // row-pass items
     int col0, ncol;    // column-pass items
@@ -58,10 +64,31 @@ __device__ __forceinline__ int owner(const BatchSurf* S, int n, int it)
         const int start = Which == 0   ? S[k].tile0
                           : Which == 1 ? S[k].row0
                           : Which == 2 ? S[k].col0
-                                       : S[k].atile0;
+                          : Which == 3 ? S[k].atile0
+                                       : S[k].dense0;
         if (it >= start) s = k;
     }
     return s;
+}
+
+// The stages run out of line so that each keeps its own register allocation
+// (the kernel's register count is the largest of them).
+template <int W>
+__device__ __noinline__ void batch_window_tile(const SpreadArgs& a, int t, float2* sm, int lane)
+{
+    if constexpr (W <= kMaxWindowWidth) window_tile<W, kTileX, kColTileY, false>(a, t, sm, lane);
+}
+
+template <int W>
+__device__ __noinline__ void batch_colored_tile(const SpreadArgs& a, int t, float2* sm, int lane)
+{
+    colored_tile<W, kTileX, kColTileY, false>(a, t, sm, lane);
+}
+
+template <int W>
+__device__ __noinline__ void batch_dense_item(const SpreadArgs& a, int it, int lane)
+{
+    if constexpr (W <= kMaxWindowWidth) window_atomic_item<W>(a, it, lane);
 }
 
 template <int L>
@@ -79,12 +106,29 @@ __device__ __forceinline__ void batch_col(const BatchSurf& s, int it, float2* sm
 
 template <int W>
 __global__ void __launch_bounds__(kBatchThreads) batch_kernel(const BatchSurf* __restrict__ S, int n,
-                                                              int ntile, int natile, int nrow,
-                                                              int ncol)
+                                                              int ntile, int ndense, int natile,
+                                                              int nrow, int ncol)
 {
     extern __shared__ __align__(16) float2 sm[];
     cg::grid_group grid = cg::this_grid();
     const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
+
+    // stage Z: the dense items accumulate with atomics: clear their bands
+    if (ndense > 0) {
+        const size_t gt = (size_t)blockIdx.x * kBatchThreads + tid;
+        const size_t gn = (size_t)gridDim.x * kBatchThreads;
+        for (int s = 0; s < n; ++s) {
+            if (S[s].ndense == 0) continue;
+            const SpreadArgs& a = S[s].sa;
+            const int w2 = a.band_ntx * (kTileX / 2);  // float4 per band row
+            const size_t total = (size_t)S[s].ra.nrows * w2;
+            float4* g4 = reinterpret_cast<float4*>(a.grid + (size_t)S[s].ra.row0 * a.nfx +
+                                                   a.band_tx0 * kTileX);
+            for (size_t i = gt; i < total; i += gn)
+                g4[(i / w2) * (a.nfx / 2) + i % w2] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        grid.sync();
+    }
 
     // stage 0a: spread of surfaces that need the atomic kernel (block items)
     float* tre = reinterpret_cast<float*>(sm);
@@ -96,11 +140,18 @@ __global__ void __launch_bounds__(kBatchThreads) batch_kernel(const BatchSurf* _
     }
     __syncthreads();
 
-    // stage 0b: conflict-free spread (warp items)
+    // stage 0b: conflict-free tiles and dense items (warp items)
     float2* wsm = sm + warp * BTile::SLOTS;
-    for (int it = blockIdx.x * kBatchWarps + warp; it < ntile; it += gridDim.x * kBatchWarps) {
-        const int s = owner<0>(S, n, it);
-        colored_tile<W, kTileX, kColTileY, false>(S[s].sa, it - S[s].tile0, wsm, lane);
+    for (int it = blockIdx.x * kBatchWarps + warp; it < ntile + ndense;
+         it += gridDim.x * kBatchWarps) {
+        if (it < ntile) {
+            const int s = owner<0>(S, n, it);
+            if (S[s].windowed) batch_window_tile<W>(S[s].sa, it - S[s].tile0, wsm, lane);
+            else batch_colored_tile<W>(S[s].sa, it - S[s].tile0, wsm, lane);
+        } else {
+            const int s = owner<4>(S, n, it - ntile);
+            batch_dense_item<W>(S[s].sa, it - ntile - S[s].dense0, lane);
+        }
     }
     grid.sync();
 
@@ -157,7 +208,7 @@ struct asfd_batch_s {
     int width = 0;
     asfd::BatchSurf* host = nullptr;  // pinned
     asfd::BatchSurf* dev = nullptr;
-    int ntile = 0, natile = 0, nrow = 0, ncol = 0;
+    int ntile = 0, ndense = 0, natile = 0, nrow = 0, ncol = 0;
     int grid_blocks = 0;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -190,7 +241,8 @@ cudaError_t launch_batch(asfd_batch_s* B, cudaStream_t st)
     cfg.numAttrs = 1;
     const BatchSurf* S = B->dev;
     const int n = (int)B->plans.size();
-    return cudaLaunchKernelEx(&cfg, batch_kernel<W>, S, n, B->ntile, B->natile, B->nrow, B->ncol);
+    return cudaLaunchKernelEx(&cfg, batch_kernel<W>, S, n, B->ntile, B->ndense, B->natile, B->nrow,
+                              B->ncol);
 }
 
 cudaError_t launch_batch_w(asfd_batch_s* B, cudaStream_t st)
@@ -274,7 +326,7 @@ asfd_status asfd_batch_create(asfd_batch* out, const asfd_params* params,
         }
         ASFD_CUDA(cudaMallocHost(&B->host, sizeof(BatchSurf) * count));
         ASFD_CUDA(cudaMalloc(&B->dev, sizeof(BatchSurf) * count));
-        int nt = 0, na = 0, nr = 0, nc = 0;
+        int nt = 0, nd = 0, na = 0, nr = 0, nc = 0;
         for (int i = 0; i < count; ++i) {
             asfd_plan_s* P = B->plans[i];
             BatchSurf& b = B->host[i];
@@ -283,11 +335,14 @@ asfd_status asfd_batch_create(asfd_batch* out, const asfd_params* params,
             b.ca = make_col_args(P, nullptr);
             b.nfx = P->nfx;
             b.nfy = P->nfy;
+            b.windowed = P->colored && P->windowed ? 1 : 0;
             const int band_tiles = (P->band_tx1 - P->band_tx0) * (P->band_ty1 - P->band_ty0);
             b.tile0 = nt;
             b.ntile = P->colored ? band_tiles * (kTileY / kColTileY) : 0;
+            b.dense0 = nd;
+            b.ndense = P->dense ? P->dense_items : 0;
             b.atile0 = na;
-            b.natile = P->colored ? 0 : band_tiles;
+            b.natile = (P->colored || P->dense) ? 0 : band_tiles;
             b.row0 = nr;
             const int row_lpc = P->nfx >= 4096 ? 1 : 4096 / P->nfx;  // RowCfg<nfx>::LPC
             b.nrow = (b.ra.nrows + row_lpc - 1) / row_lpc;
@@ -295,11 +350,13 @@ asfd_status asfd_batch_create(asfd_batch* out, const asfd_params* params,
             b.col0 = nc;
             b.ncol = (P->prm.m2x + col_lpc - 1) / col_lpc;
             nt += b.ntile;
+            nd += b.ndense;
             na += b.natile;
             nr += b.nrow;
             nc += b.ncol;
         }
         B->ntile = nt;
+        B->ndense = nd;
         B->natile = na;
         B->nrow = nr;
         B->ncol = nc;
@@ -385,7 +442,7 @@ asfd_status asfd_batch_get_info(asfd_batch B, asfd_batch_info* info)
     info->surfaces = (int)B->plans.size();
     info->blocks = B->grid_blocks;
     info->threads_per_block = kBatchThreads;
-    info->spread_items = B->ntile + B->natile;
+    info->spread_items = B->ntile + B->ndense + B->natile;
     info->row_items = B->nrow;
     info->col_items = B->ncol;
     info->graph = B->graph_ok ? 1 : 0;

@@ -333,6 +333,8 @@ asfd_status plan_validate(const asfd_params* p, int* nfx, int* nfy, double* beta
             return fail(ASFD_ERR_ARG, "pitches, wavelength, z0 and sigma must be finite and > 0");
     if (p->kernel_width < 2 || p->kernel_width > 16)
         return fail(ASFD_ERR_UNSUPPORTED, "kernel_width must be in [2, 16]");
+    if (p->deterministic != 0 && p->deterministic != 1)
+        return fail(ASFD_ERR_ARG, "deterministic must be 0 or 1");
     if (p->kind != ASFD_KERNEL_ES && p->kind != ASFD_KERNEL_LEARNED)
         return fail(ASFD_ERR_ARG, "kind must be ASFD_KERNEL_ES or ASFD_KERNEL_LEARNED");
     if (p->kind == ASFD_KERNEL_LEARNED && p->kernel_width != kLearnW)
@@ -587,6 +589,7 @@ asfd_status plan_build_colored(asfd_plan_s* P, bool wraps, cudaStream_t st)
     for (int nx = 0; nx < p.n1x; ++nx) spread_x = std::max(spread_x, cr[2 * nx + 1] - cr[2 * nx]);
     P->col_spread_x = spread_x;
     P->windowed = false;
+    P->dense = false;
     if (p.n1x < 2) msx = 1e30;
     if (p.n1y < 2) msy = 1e30;
     P->min_step_x = msx;
@@ -598,6 +601,19 @@ asfd_status plan_build_colored(asfd_plan_s* P, bool wraps, cudaStream_t st)
     if (wraps || !(msx > 1e-3) || !(msy > 1e-3) || P->w > kMaxRingWidth) return ASFD_OK;
     const double sxd = std::ceil((P->w + margin) / msx);
     const double hd = std::ceil((P->w + spread_y + margin) / msy);
+    // the register-window kernels also need columns w apart across rows
+    const double sxw = std::ceil((P->w + spread_x + margin) / msx);
+    if (P->w <= kMaxWindowWidth && p.kind == ASFD_KERNEL_ES && !p.deterministic) {
+        // register windows flushed to the fine grid with float atomics (the
+        // fastest path, and the only efficient one for dense maps); runs of
+        // dense_rows rows per lane, enough warp items to fill the GPU
+        const long long ncb = (p.n1x + 31) / 32;
+        const long long rows = std::max<long long>(8, std::min<long long>(256, p.n1y * ncb / 2432));
+        P->dense_rows = (int)rows;
+        P->dense_items = (int)(ncb * ((p.n1y + rows - 1) / rows));
+        P->dense = true;
+        return ASFD_OK;
+    }
     // beyond 64 samples between lanes (samples packed far below one cell
     // apart) few lanes find work in a tile and the atomic kernel is faster
     if (!(sxd <= 64.0) || !(hd <= 64.0)) return ASFD_OK;
@@ -646,9 +662,7 @@ asfd_status plan_build_colored(asfd_plan_s* P, bool wraps, cudaStream_t st)
     P->sx_min = (int)sxd;
     P->h_min = (int)hd;
     P->colored = true;
-    // the register-window kernel also needs columns w apart across rows
-    const double sxw = std::ceil((P->w + spread_x + margin) / msx);
-    if (P->w <= kMaxWindowWidth && sxw <= 64.0) {
+    if (P->w <= kMaxWindowWidth) {
         P->sxw_min = (int)sxw;
         P->windowed = true;
     }

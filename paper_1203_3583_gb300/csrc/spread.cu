@@ -56,6 +56,18 @@ template <int W>
 cudaError_t launch_w(const SpreadArgs& a, int tiles, bool colored, bool windowed, cudaStream_t st)
 {
     if constexpr (W <= kMaxWindowWidth) {
+        if (a.dense_rows > 0) {
+            // the dense kernel accumulates with atomics: zero the band first
+            const size_t pitch = sizeof(float2) * (size_t)a.nfx;
+            const int c0 = a.band_tx0 * kTileX, r0 = a.band_ty0 * kTileY;
+            const size_t width = sizeof(float2) * (size_t)a.band_ntx * kTileX;
+            const size_t height = (size_t)(tiles / a.band_ntx) * kTileY;
+            cudaError_t e = cudaMemset2DAsync(a.grid + (size_t)r0 * a.nfx + c0, pitch, 0, width,
+                                              height, st);
+            if (e != cudaSuccess) return e;
+            spread_es_dense_kernel<W><<<(a.dense_items + 3) / 4, 128, 0, st>>>(a, a.dense_items);
+            return cudaGetLastError();
+        }
         if (windowed) {
             spread_es_window_kernel<W, kTileX, kColTileY, false>
                 <<<tiles * (kTileY / kColTileY), 32, 0, st>>>(a);
@@ -110,6 +122,8 @@ SpreadArgs make_spread_args(const asfd_plan_s* P, const float2* u1)
     a.sx_min = P->sx_min;
     a.h_min = P->h_min;
     a.sxw_min = P->sxw_min;
+    a.dense_rows = P->dense ? P->dense_rows : 0;
+    a.dense_items = P->dense ? P->dense_items : 0;
     a.half_w = 0.5f * (float)P->w;
     a.beta_log2e = (float)(P->beta * 1.4426950408889634074);
     a.two_over_w = (float)(2.0 / P->w);

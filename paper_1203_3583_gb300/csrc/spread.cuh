@@ -25,6 +25,8 @@ struct SpreadArgs {
     int band_tx0, band_ty0, band_ntx;
     int sx_min, h_min;
     int sxw_min;       // column stride of the register-window kernel
+    int dense_rows;    // rows per run of the dense (global-atomic) window kernel (0: not used)
+    int dense_items;   // its warp items (32 columns x dense_rows rows each)
     float half_w;      // w/2
     float beta_log2e;  // beta * log2(e)
     float two_over_w;  // 2/w
@@ -222,6 +224,68 @@ __device__ __forceinline__ float2 es_weight2_fast(float2 z, float neg_c2, float 
     return e;
 }
 
+// Adds one sample to a register window whose top row is R0 and whose first
+// column is X0: fresh (the window is empty: overwrite every slot), or with
+// its first tap row dn = 0, 1 or 2 rows below R0 (the dn top rows go to
+// flush(b) first and the rest move up by dn inside the FMAs).  offn is the
+// sample's first tap column minus X0 (0, or 1 with a spare column).
+template <int W, int WX, class Flush>
+__device__ __forceinline__ void window_add(float2 (&acc)[W][WX], bool fresh, int dn, int offn,
+                                           float dx, float dy, float2 c, const SpreadArgs& a,
+                                           float neg_c2, Flush&& flush)
+{
+    float wy[W], wxe[WX];
+    const float by = dy - a.half_w;
+    const float bx = dx - a.half_w - (float)offn;
+#pragma unroll
+    for (int b = 0; b < W; ++b) {
+        const float2 e = es_weight2_fast(make_float2(by + (float)b, bx + (float)b), neg_c2,
+                                         a.beta_log2e);
+        wy[b] = e.x;
+        wxe[b] = e.y;
+    }
+    if constexpr (WX > W) {
+        wxe[W] = es_weight_fast(bx + (float)W, a.two_over_w, a.beta_log2e);
+        // tap column i of the sample sits in window column i + offn
+        if (offn == 1) wxe[0] = 0.f;
+        else wxe[W] = 0.f;
+    }
+    if (fresh) {
+#pragma unroll
+        for (int b = 0; b < W; ++b) {
+            const float2 cb = mul2(c, wy[b]);
+#pragma unroll
+            for (int i = 0; i < WX; ++i) acc[b][i] = mul2(cb, wxe[i]);
+        }
+    } else if (dn == 0) {
+#pragma unroll
+        for (int b = 0; b < W; ++b) {
+            const float2 cb = mul2(c, wy[b]);
+#pragma unroll
+            for (int i = 0; i < WX; ++i) acc[b][i] = fma2(cb, wxe[i], acc[b][i]);
+        }
+    } else if (dn == 1) {
+        flush(0);
+#pragma unroll
+        for (int b = 0; b < W; ++b) {
+            const float2 cb = mul2(c, wy[b]);
+#pragma unroll
+            for (int i = 0; i < WX; ++i)
+                acc[b][i] = (b + 1 < W) ? fma2(cb, wxe[i], acc[b + 1][i]) : mul2(cb, wxe[i]);
+        }
+    } else {
+        flush(0);
+        flush(1);
+#pragma unroll
+        for (int b = 0; b < W; ++b) {
+            const float2 cb = mul2(c, wy[b]);
+#pragma unroll
+            for (int i = 0; i < WX; ++i)
+                acc[b][i] = (b + 2 < W) ? fma2(cb, wxe[i], acc[b + 2][i]) : mul2(cb, wxe[i]);
+        }
+    }
+}
+
 template <int W, int TX, int TY, bool TAB>
 __device__ __forceinline__ void window_tile(const SpreadArgs& a, int t, float2* tile, int lane)
 {
@@ -348,61 +412,12 @@ __device__ __forceinline__ void window_tile(const SpreadArgs& a, int t, float2* 
                     R0 = l0y;
                     live = true;
                 }
-                const int offn = l0x - X0;
-                const int dn = l0y - R0;
                 const float2 c = sample_value_fast(ua, ex, ey, qa);
-                float wy[W], wxe[WX];
-                const float by = dy - a.half_w;
-                const float bx = dx - a.half_w - (float)offn;
-#pragma unroll
-                for (int b = 0; b < W; ++b) {
-                    const float2 e = es_weight2_fast(make_float2(by + (float)b, bx + (float)b),
-                                                     neg_c2, a.beta_log2e);
-                    wy[b] = e.x;
-                    wxe[b] = e.y;
-                }
-                if constexpr (WX > W) {
-                    wxe[W] = es_weight_fast(bx + (float)W, a.two_over_w, a.beta_log2e);
-                    // tap column i of the sample sits in window column i + offn
-                    if (offn == 1) wxe[0] = 0.f;
-                    else wxe[W] = 0.f;
-                }
-                if (fresh) {
-#pragma unroll
-                    for (int b = 0; b < W; ++b) {
-                        const float2 cb = mul2(c, wy[b]);
-#pragma unroll
-                        for (int i = 0; i < WX; ++i) acc[b][i] = mul2(cb, wxe[i]);
-                    }
-                } else if (dn == 0) {
-#pragma unroll
-                    for (int b = 0; b < W; ++b) {
-                        const float2 cb = mul2(c, wy[b]);
-#pragma unroll
-                        for (int i = 0; i < WX; ++i) acc[b][i] = fma2(cb, wxe[i], acc[b][i]);
-                    }
-                } else if (dn == 1) {
-                    window_flush<WX, TX, TY>(tile, R0 - oy, X0 - ox, cmask, acc[0]);
-#pragma unroll
-                    for (int b = 0; b < W; ++b) {
-                        const float2 cb = mul2(c, wy[b]);
-#pragma unroll
-                        for (int i = 0; i < WX; ++i)
-                            acc[b][i] = (b + 1 < W) ? fma2(cb, wxe[i], acc[b + 1][i])
-                                                    : mul2(cb, wxe[i]);
-                    }
-                } else {
-                    window_flush<WX, TX, TY>(tile, R0 - oy, X0 - ox, cmask, acc[0]);
-                    window_flush<WX, TX, TY>(tile, R0 + 1 - oy, X0 - ox, cmask, acc[1]);
-#pragma unroll
-                    for (int b = 0; b < W; ++b) {
-                        const float2 cb = mul2(c, wy[b]);
-#pragma unroll
-                        for (int i = 0; i < WX; ++i)
-                            acc[b][i] = (b + 2 < W) ? fma2(cb, wxe[i], acc[b + 2][i])
-                                                    : mul2(cb, wxe[i]);
-                    }
-                }
+                window_add<W, WX>(acc, fresh, l0y - R0, l0x - X0, dx, dy, c, a, neg_c2,
+                                  [&](int b) {
+                                      window_flush<WX, TX, TY>(tile, R0 + b - oy, X0 - ox, cmask,
+                                                               acc[b]);
+                                  });
                 R0 = l0y;
             }
             __syncwarp();
@@ -434,6 +449,94 @@ __global__ void __launch_bounds__(32) spread_es_window_kernel(SpreadArgs a)
 {
     __shared__ __align__(16) float2 tile[ColoredTile<TX, TY>::SLOTS];
     window_tile<W, TX, TY, TAB>(a, blockIdx.x, tile, threadIdx.x);
+}
+
+// Dense maps (many samples per fine-grid cell, where conflict-free lanes
+// would have to be many columns apart): warp item `it` takes 32 consecutive
+// source columns (one per lane) over `dense_rows` consecutive rows; each lane
+// walks its column with the register window above, and window rows go
+// straight to the fine grid with float2 atomic adds (which only need the
+// band zeroed beforehand).  Consecutive samples of a column share their
+// first tap row about 1/(alpha (1 + q)) times, so a row is flushed about
+// alpha times per sample.  Lanes need no step synchronisation.
+template <int W>
+__device__ __forceinline__ void window_atomic_item(const SpreadArgs& a, int it, int lane)
+{
+    constexpr int WX = W + kWindowSpare;
+    const int ncb = (a.n1x + 31) / 32;
+    const int nx = (it % ncb) * 32 + lane;
+    const int ny0 = (it / ncb) * a.dense_rows;
+    const int nyl = min(ny0 + a.dense_rows, a.n1y) - 1;
+    if (nx >= a.n1x || ny0 > nyl) return;
+    const int mx = a.nfx - 1, my = a.nfy - 1;
+    const float neg_c2 = -a.two_over_w * a.two_over_w;
+    const AxisEntry ex = a.ax[nx];
+    const AxisPos px = a.px[nx];
+
+    // window columns: first tap columns of the run's first and last samples
+    int X0, maxoff;
+    {
+        int lf, ll, yy;
+        float f0, f1;
+        sample_pos(ex, a.ay[ny0], px, a.py[ny0], __ldg(&a.q[(size_t)ny0 * a.n1x + nx]), a.half_w,
+                   lf, yy, f0, f1);
+        sample_pos(ex, a.ay[nyl], px, a.py[nyl], __ldg(&a.q[(size_t)nyl * a.n1x + nx]), a.half_w,
+                   ll, yy, f0, f1);
+        X0 = (kWindowSpare > 0) ? min(lf, ll) : lf;
+        maxoff = (kWindowSpare > 0 && lf != ll) ? 1 : 0;
+    }
+    float2 acc[W][WX];
+    int R0 = 0;
+    bool live = false;
+    auto flush_row = [&](int b) {
+        float2* row = a.grid + (size_t)((R0 + b) & my) * a.nfx;
+#pragma unroll
+        for (int i = 0; i < WX; ++i)
+            if (i < W + maxoff) atomicAdd(row + ((X0 + i) & mx), acc[b][i]);
+    };
+    float qn = __ldg(&a.q[(size_t)ny0 * a.n1x + nx]);
+    float2 un = __ldg(&a.u1[(size_t)ny0 * a.n1x + nx]);
+    for (int ny = ny0; ny <= nyl; ++ny) {
+        const float q = qn;
+        const float2 u = un;
+        if (ny < nyl) {
+            qn = __ldg(&a.q[(size_t)(ny + 1) * a.n1x + nx]);
+            un = __ldg(&a.u1[(size_t)(ny + 1) * a.n1x + nx]);
+        }
+        const AxisEntry ey = a.ay[ny];
+        int l0x, l0y;
+        float dx, dy;
+        sample_pos(ex, ey, px, a.py[ny], q, a.half_w, l0x, l0y, dx, dy);
+        const int off = l0x - X0, d = l0y - R0;
+        if (live && (off < 0 || off > maxoff || d < 0 || d > 2)) {
+#pragma unroll
+            for (int b = 0; b < W; ++b) flush_row(b);
+            live = false;
+        }
+        const bool fresh = !live;
+        if (fresh) {
+            if (off < 0 || off > maxoff) {
+                X0 = l0x;
+                maxoff = 0;
+            }
+            R0 = l0y;
+            live = true;
+        }
+        const float2 c = sample_value_fast(u, ex, ey, q);
+        window_add<W, WX>(acc, fresh, l0y - R0, l0x - X0, dx, dy, c, a, neg_c2, flush_row);
+        R0 = l0y;
+    }
+    if (live) {
+#pragma unroll
+        for (int b = 0; b < W; ++b) flush_row(b);
+    }
+}
+
+template <int W>
+__global__ void __launch_bounds__(128) spread_es_dense_kernel(SpreadArgs a, int items)
+{
+    const int it = blockIdx.x * 4 + threadIdx.x / 32;
+    if (it < items) window_atomic_item<W>(a, it, threadIdx.x % 32);
 }
 
 // Fallback spread of band tile `tile` (kTileX x kTileY) by a whole block:

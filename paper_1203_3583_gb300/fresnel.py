@@ -27,7 +27,8 @@ class FresnelPlan:
     """Plan for Eq. 8 of the paper on one GPU (see include/asfd.h)."""
 
     def __init__(self, geometry: dict, d1, sigma: float = 2.0, kernel_width: int = 7,
-                 es_beta: float = 0.0, stream=None, kind: str = "es"):
+                 es_beta: float = 0.0, stream=None, kind: str = "es",
+                 deterministic: bool = False):
         self.geometry = dict(geometry)
         if kind not in ("es", "learned"):
             raise ValueError("kind must be 'es' or 'learned'")
@@ -36,7 +37,8 @@ class FresnelPlan:
             kernel_width = 4
         self.params = capi.make_params(
             geometry, sigma=sigma, kernel_width=kernel_width, es_beta=es_beta,
-            kind=capi.ASFD_KERNEL_LEARNED if kind == "learned" else capi.ASFD_KERNEL_ES)
+            kind=capi.ASFD_KERNEL_LEARNED if kind == "learned" else capi.ASFD_KERNEL_ES,
+            deterministic=deterministic)
         self.shape1 = (int(geometry["n1y"]), int(geometry["n1x"]))
         self.shape2 = (int(geometry["m2y"]), int(geometry["m2x"]))
         self._handle = None
@@ -107,11 +109,13 @@ class FresnelPlan:
 class FresnelBatch:
     """Many surfaces in one persistent kernel per call (see asfd_batch_create)."""
 
-    def __init__(self, items, kernel_width: int = 7, sigma: float = 2.0, stream=None):
+    def __init__(self, items, kernel_width: int = 7, sigma: float = 2.0, stream=None,
+                 deterministic: bool = False):
         """items: list of (geometry, d1)."""
         self.shapes1 = [(int(g["n1y"]), int(g["n1x"])) for g, _ in items]
         self.shapes2 = [(int(g["m2y"]), int(g["m2x"])) for g, _ in items]
-        params = [capi.make_params(g, sigma=sigma, kernel_width=kernel_width) for g, _ in items]
+        params = [capi.make_params(g, sigma=sigma, kernel_width=kernel_width,
+                                   deterministic=deterministic) for g, _ in items]
         d1s = [_as_cuda_f64(d1) for _, d1 in items]
         self._handle = capi.asfd_batch_create(params, d1s, stream)
 

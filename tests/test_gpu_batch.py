@@ -76,3 +76,18 @@ def test_batch_matches_oracle(rgb_batch):
         ref = oracle.eq7(g, u1, d1, points=pts)
         err = rel_l2(out[i][pts[1], pts[0]], ref)
         assert err < 1e-5, (i, err)
+
+
+def test_deterministic_batch_equals_individual_plans():
+    """With deterministic=True every surface takes atomic-free spreading (or
+    shared-memory atomics where the map needs them); the batch still equals
+    the surfaces' own plans."""
+    items = W.make_batch()[:8]
+    with FresnelBatch([(g, d1) for g, _, d1 in items], deterministic=True) as b:
+        out = b.execute([torch.as_tensor(u, device="cuda") for _, u, _ in items])
+        torch.cuda.synchronize()
+        got = [o.cpu().numpy() for o in out]
+    for i, (g, u1, d1) in enumerate(items):
+        with FresnelPlan(g, d1, deterministic=True) as p:
+            ref = p.execute(torch.as_tensor(u1, device="cuda")).cpu().numpy()
+        assert rel_l2(got[i], ref) < 5e-6, i
