@@ -603,7 +603,7 @@ asfd_status plan_build_colored(asfd_plan_s* P, bool wraps, cudaStream_t st)
     const double hd = std::ceil((P->w + spread_y + margin) / msy);
     // the register-window kernels also need columns w apart across rows
     const double sxw = std::ceil((P->w + spread_x + margin) / msx);
-    if (P->w <= kMaxWindowWidth && p.kind == ASFD_KERNEL_ES && !p.deterministic) {
+    if (P->w <= kMaxWindowWidth && !p.deterministic) {
         // register windows flushed to the fine grid with float atomics (the
         // fastest path, and the only efficient one for dense maps); runs of
         // dense_rows rows per lane, enough warp items to fill the GPU

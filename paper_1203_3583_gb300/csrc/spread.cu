@@ -52,22 +52,25 @@ __global__ void __launch_bounds__(256) spread_es_atomic_kernel(SpreadArgs a)
     atomic_tile<W, TAB>(a, blockIdx.x, tre, tim, threadIdx.x, blockDim.x);
 }
 
+// The dense kernels accumulate with atomic adds: clear the band, then launch.
+template <int W, bool TAB>
+cudaError_t launch_dense(const SpreadArgs& a, int tiles, cudaStream_t st)
+{
+    const size_t pitch = sizeof(float2) * (size_t)a.nfx;
+    const int c0 = a.band_tx0 * kTileX, r0 = a.band_ty0 * kTileY;
+    const size_t width = sizeof(float2) * (size_t)a.band_ntx * kTileX;
+    const size_t height = (size_t)(tiles / a.band_ntx) * kTileY;
+    cudaError_t e = cudaMemset2DAsync(a.grid + (size_t)r0 * a.nfx + c0, pitch, 0, width, height, st);
+    if (e != cudaSuccess) return e;
+    spread_es_dense_kernel<W, TAB><<<(a.dense_items + 3) / 4, 128, 0, st>>>(a, a.dense_items);
+    return cudaGetLastError();
+}
+
 template <int W>
 cudaError_t launch_w(const SpreadArgs& a, int tiles, bool colored, bool windowed, cudaStream_t st)
 {
     if constexpr (W <= kMaxWindowWidth) {
-        if (a.dense_rows > 0) {
-            // the dense kernel accumulates with atomics: zero the band first
-            const size_t pitch = sizeof(float2) * (size_t)a.nfx;
-            const int c0 = a.band_tx0 * kTileX, r0 = a.band_ty0 * kTileY;
-            const size_t width = sizeof(float2) * (size_t)a.band_ntx * kTileX;
-            const size_t height = (size_t)(tiles / a.band_ntx) * kTileY;
-            cudaError_t e = cudaMemset2DAsync(a.grid + (size_t)r0 * a.nfx + c0, pitch, 0, width,
-                                              height, st);
-            if (e != cudaSuccess) return e;
-            spread_es_dense_kernel<W><<<(a.dense_items + 3) / 4, 128, 0, st>>>(a, a.dense_items);
-            return cudaGetLastError();
-        }
+        if (a.dense_rows > 0) return launch_dense<W, false>(a, tiles, st);
         if (windowed) {
             spread_es_window_kernel<W, kTileX, kColTileY, false>
                 <<<tiles * (kTileY / kColTileY), 32, 0, st>>>(a);
@@ -88,6 +91,7 @@ cudaError_t launch_w(const SpreadArgs& a, int tiles, bool colored, bool windowed
 
 cudaError_t launch_table(const SpreadArgs& a, int tiles, bool colored, cudaStream_t st)
 {
+    if (a.dense_rows > 0) return launch_dense<kLearnW, true>(a, tiles, st);
     if (colored)
         spread_es_colored_kernel<kLearnW, kTileX, kColTileY, true>
             <<<tiles * (kTileY / kColTileY), 32, 0, st>>>(a);

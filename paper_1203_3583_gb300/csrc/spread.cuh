@@ -286,6 +286,82 @@ __device__ __forceinline__ void window_add(float2 (&acc)[W][WX], bool fresh, int
     }
 }
 
+// window_add with the W x and W y tap weights given (learned tables): the
+// window column i takes tap i - offn.
+template <int W, int WX, class Flush>
+__device__ __forceinline__ void window_add_w(float2 (&acc)[W][WX], bool fresh, int dn, int offn,
+                                             const float (&wx)[W], const float (&wy)[W], float2 c,
+                                             Flush&& flush)
+{
+    float wxe[WX];
+#pragma unroll
+    for (int i = 0; i < WX; ++i) {
+        const float lo = (i < W) ? wx[i] : 0.f;
+        const float hi = (i >= 1 && i - 1 < W) ? wx[i - 1] : 0.f;
+        wxe[i] = offn == 1 ? hi : lo;
+    }
+    if (fresh) {
+#pragma unroll
+        for (int b = 0; b < W; ++b) {
+            const float2 cb = mul2(c, wy[b]);
+#pragma unroll
+            for (int i = 0; i < WX; ++i) acc[b][i] = mul2(cb, wxe[i]);
+        }
+    } else if (dn == 0) {
+#pragma unroll
+        for (int b = 0; b < W; ++b) {
+            const float2 cb = mul2(c, wy[b]);
+#pragma unroll
+            for (int i = 0; i < WX; ++i) acc[b][i] = fma2(cb, wxe[i], acc[b][i]);
+        }
+    } else if (dn == 1) {
+        flush(0);
+#pragma unroll
+        for (int b = 0; b < W; ++b) {
+            const float2 cb = mul2(c, wy[b]);
+#pragma unroll
+            for (int i = 0; i < WX; ++i)
+                acc[b][i] = (b + 1 < W) ? fma2(cb, wxe[i], acc[b + 1][i]) : mul2(cb, wxe[i]);
+        }
+    } else {
+        flush(0);
+        flush(1);
+#pragma unroll
+        for (int b = 0; b < W; ++b) {
+            const float2 cb = mul2(c, wy[b]);
+#pragma unroll
+            for (int i = 0; i < WX; ++i)
+                acc[b][i] = (b + 2 < W) ? fma2(cb, wxe[i], acc[b + 2][i]) : mul2(cb, wxe[i]);
+        }
+    }
+}
+
+// Horner evaluation of the learned tap polynomials of one source tile staged
+// in shared memory as (x, y) coefficient pairs [tap][coef] (kLearnCoef
+// coefficients per tap, in t = 2 d - 1); both axes at once in FP32x2.
+template <int W>
+__device__ __forceinline__ void table_weights_smem(const float4* tab, float dx, float dy,
+                                                   float (&wx)[W], float (&wy)[W])
+{
+    static_assert(kLearnCoef == 8, "four float4 per tap");
+    const float2 t = make_float2(fmaf(2.0f, dx, -1.0f), fmaf(2.0f, dy, -1.0f));
+#pragma unroll
+    for (int i = 0; i < W; ++i) {
+        const float4 c01 = tab[4 * i], c23 = tab[4 * i + 1], c45 = tab[4 * i + 2],
+                     c67 = tab[4 * i + 3];
+        float2 p = make_float2(c67.z, c67.w);
+        p = fma2v(p, t, make_float2(c67.x, c67.y));
+        p = fma2v(p, t, make_float2(c45.z, c45.w));
+        p = fma2v(p, t, make_float2(c45.x, c45.y));
+        p = fma2v(p, t, make_float2(c23.z, c23.w));
+        p = fma2v(p, t, make_float2(c23.x, c23.y));
+        p = fma2v(p, t, make_float2(c01.z, c01.w));
+        p = fma2v(p, t, make_float2(c01.x, c01.y));
+        wx[i] = p.x;
+        wy[i] = p.y;
+    }
+}
+
 template <int W, int TX, int TY, bool TAB>
 __device__ __forceinline__ void window_tile(const SpreadArgs& a, int t, float2* tile, int lane)
 {
@@ -459,28 +535,39 @@ __global__ void __launch_bounds__(32) spread_es_window_kernel(SpreadArgs a)
 // band zeroed beforehand).  Consecutive samples of a column share their
 // first tap row about 1/(alpha (1 + q)) times, so a row is flushed about
 // alpha times per sample.  Lanes need no step synchronisation.
-template <int W>
-__device__ __forceinline__ void window_atomic_item(const SpreadArgs& a, int it, int lane)
+template <int W, bool TAB = false>
+__device__ __forceinline__ void window_atomic_item(const SpreadArgs& a, int it, int lane,
+                                                   float4* tsm = nullptr)
 {
     constexpr int WX = W + kWindowSpare;
     const int ncb = (a.n1x + 31) / 32;
     const int nx = (it % ncb) * 32 + lane;
     const int ny0 = (it / ncb) * a.dense_rows;
     const int nyl = min(ny0 + a.dense_rows, a.n1y) - 1;
-    if (nx >= a.n1x || ny0 > nyl) return;
+    if constexpr (TAB) {
+        // learned kernel: the warp's lanes span two source-tile columns and
+        // step through the same rows, so the two tiles' polynomial tables
+        // are staged in shared memory (tsm: 2 x 4W float4) per tile row
+        if (ny0 > nyl || (it % ncb) * 32 >= a.n1x) return;  // warp-uniform
+    } else {
+        if (nx >= a.n1x || ny0 > nyl) return;
+    }
+    // (learned kernel: lanes past the last column follow along without flushing)
+    const bool lane_on = !TAB || nx < a.n1x;
+    const int nxc = (!TAB || lane_on) ? nx : a.n1x - 1;
     const int mx = a.nfx - 1, my = a.nfy - 1;
     const float neg_c2 = -a.two_over_w * a.two_over_w;
-    const AxisEntry ex = a.ax[nx];
-    const AxisPos px = a.px[nx];
+    const AxisEntry ex = a.ax[nxc];
+    const AxisPos px = a.px[nxc];
 
     // window columns: first tap columns of the run's first and last samples
     int X0, maxoff;
     {
         int lf, ll, yy;
         float f0, f1;
-        sample_pos(ex, a.ay[ny0], px, a.py[ny0], __ldg(&a.q[(size_t)ny0 * a.n1x + nx]), a.half_w,
+        sample_pos(ex, a.ay[ny0], px, a.py[ny0], __ldg(&a.q[(size_t)ny0 * a.n1x + nxc]), a.half_w,
                    lf, yy, f0, f1);
-        sample_pos(ex, a.ay[nyl], px, a.py[nyl], __ldg(&a.q[(size_t)nyl * a.n1x + nx]), a.half_w,
+        sample_pos(ex, a.ay[nyl], px, a.py[nyl], __ldg(&a.q[(size_t)nyl * a.n1x + nxc]), a.half_w,
                    ll, yy, f0, f1);
         X0 = (kWindowSpare > 0) ? min(lf, ll) : lf;
         maxoff = (kWindowSpare > 0 && lf != ll) ? 1 : 0;
@@ -492,16 +579,29 @@ __device__ __forceinline__ void window_atomic_item(const SpreadArgs& a, int it, 
         float2* row = a.grid + (size_t)((R0 + b) & my) * a.nfx;
 #pragma unroll
         for (int i = 0; i < WX; ++i)
-            if (i < W + maxoff) atomicAdd(row + ((X0 + i) & mx), acc[b][i]);
+            if (lane_on && i < W + maxoff) atomicAdd(row + ((X0 + i) & mx), acc[b][i]);
     };
-    float qn = __ldg(&a.q[(size_t)ny0 * a.n1x + nx]);
-    float2 un = __ldg(&a.u1[(size_t)ny0 * a.n1x + nx]);
+    float qn = __ldg(&a.q[(size_t)ny0 * a.n1x + nxc]);
+    float2 un = __ldg(&a.u1[(size_t)ny0 * a.n1x + nxc]);
+    int tab_ty = -1;
+    const int tcol0 = ((it % ncb) * 32) / kSrcTile;  // first source-tile column of the warp
+    // the table float4 this lane stages, loaded one tile row ahead
+    const int tcol = min(tcol0 + lane / (4 * W), a.nstx - 1);
+    auto load_tab = [&](int ty) {
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (TAB && lane < 8 * W && ty * kSrcTile < a.n1y)
+            v = __ldg(reinterpret_cast<const float4*>(a.table + ((size_t)ty * a.nstx + tcol) *
+                                                                   kLearnTableSize) +
+                      lane % (4 * W));
+        return v;
+    };
+    float4 tnext = load_tab(ny0 / kSrcTile);
     for (int ny = ny0; ny <= nyl; ++ny) {
         const float q = qn;
         const float2 u = un;
         if (ny < nyl) {
-            qn = __ldg(&a.q[(size_t)(ny + 1) * a.n1x + nx]);
-            un = __ldg(&a.u1[(size_t)(ny + 1) * a.n1x + nx]);
+            qn = __ldg(&a.q[(size_t)(ny + 1) * a.n1x + nxc]);
+            un = __ldg(&a.u1[(size_t)(ny + 1) * a.n1x + nxc]);
         }
         const AxisEntry ey = a.ay[ny];
         int l0x, l0y;
@@ -523,7 +623,31 @@ __device__ __forceinline__ void window_atomic_item(const SpreadArgs& a, int it, 
             live = true;
         }
         const float2 c = sample_value_fast(u, ex, ey, q);
-        window_add<W, WX>(acc, fresh, l0y - R0, l0x - X0, dx, dy, c, a, neg_c2, flush_row);
+        if constexpr (TAB) {
+            if (ny / kSrcTile != tab_ty) {  // warp-uniform: every lane is on row ny
+                tab_ty = ny / kSrcTile;
+                __syncwarp();
+                // global layout [axis][tap][coef]; staged as [tap][coef] pairs
+                // (x, y) so that the Horner steps read ready FP32x2 operands
+                if (lane < 8 * W) {
+                    const int e = lane % (4 * W);  // float4 index within the tile's table
+                    const float4 v = tnext;
+                    const int axis = e / (2 * W), k0 = (e % (2 * W)) * 4;  // tap * 8 + coef
+                    float* d = reinterpret_cast<float*>(tsm + (lane / (4 * W)) * (4 * W)) + axis;
+                    d[2 * (k0 + 0)] = v.x;
+                    d[2 * (k0 + 1)] = v.y;
+                    d[2 * (k0 + 2)] = v.z;
+                    d[2 * (k0 + 3)] = v.w;
+                }
+                __syncwarp();
+                tnext = load_tab(tab_ty + 1);
+            }
+            float wx[W], wy[W];
+            table_weights_smem<W>(tsm + (nxc / kSrcTile - tcol0) * (4 * W), dx, dy, wx, wy);
+            window_add_w<W, WX>(acc, fresh, l0y - R0, l0x - X0, wx, wy, c, flush_row);
+        } else {
+            window_add<W, WX>(acc, fresh, l0y - R0, l0x - X0, dx, dy, c, a, neg_c2, flush_row);
+        }
         R0 = l0y;
     }
     if (live) {
@@ -532,11 +656,12 @@ __device__ __forceinline__ void window_atomic_item(const SpreadArgs& a, int it, 
     }
 }
 
-template <int W>
+template <int W, bool TAB = false>
 __global__ void __launch_bounds__(128) spread_es_dense_kernel(SpreadArgs a, int items)
 {
+    __shared__ float4 tsm[4][TAB ? 8 * W : 1];
     const int it = blockIdx.x * 4 + threadIdx.x / 32;
-    if (it < items) window_atomic_item<W>(a, it, threadIdx.x % 32);
+    if (it < items) window_atomic_item<W, TAB>(a, it, threadIdx.x % 32, tsm[threadIdx.x / 32]);
 }
 
 // Fallback spread of band tile `tile` (kTileX x kTileY) by a whole block:
