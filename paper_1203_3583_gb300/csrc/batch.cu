@@ -86,9 +86,9 @@ __device__ __noinline__ void batch_colored_tile(const SpreadArgs& a, int t, floa
 }
 
 template <int W>
-__device__ __noinline__ void batch_dense_item(const SpreadArgs& a, int it, int lane)
+__device__ __noinline__ void batch_dense_item(const SpreadArgs& a, int it, int lane, char* ring)
 {
-    if constexpr (W <= kMaxWindowWidth) window_atomic_item<W>(a, it, lane);
+    if constexpr (W <= kMaxWindowWidth) window_atomic_item<W>(a, it, lane, ring);
 }
 
 template <int L>
@@ -150,7 +150,8 @@ __global__ void __launch_bounds__(kBatchThreads) batch_kernel(const BatchSurf* _
             else batch_colored_tile<W>(S[s].sa, it - S[s].tile0, wsm, lane);
         } else {
             const int s = owner<4>(S, n, it - ntile);
-            batch_dense_item<W>(S[s].sa, it - ntile - S[s].dense0, lane);
+            batch_dense_item<W>(S[s].sa, it - ntile - S[s].dense0, lane,
+                                reinterpret_cast<char*>(wsm));
         }
     }
     grid.sync();

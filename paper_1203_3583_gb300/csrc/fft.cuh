@@ -31,16 +31,54 @@ __device__ __forceinline__ constexpr float cos16(int j)
 }
 __device__ __forceinline__ constexpr float sin16(int j) { return cos16(j - 4); }
 
-__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+// Complex arithmetic on packed FP32x2 registers (add/sub/mul/fma .f32x2):
+// one instruction per complex add, two per complex multiply, with the same
+// IEEE rounding per component as the scalar forms.
+__device__ __forceinline__ unsigned long long f2_bits(float2 v)
+{
+    return *reinterpret_cast<const unsigned long long*>(&v);
+}
+__device__ __forceinline__ float2 f2_from(unsigned long long r)
+{
+    return *reinterpret_cast<const float2*>(&r);
+}
+__device__ __forceinline__ float2 cadd(float2 a, float2 b)
+{
+    unsigned long long r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(f2_bits(a)), "l"(f2_bits(b)));
+    return f2_from(r);
+}
+__device__ __forceinline__ float2 csub(float2 a, float2 b)
+{
+    unsigned long long r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(f2_bits(a)), "l"(f2_bits(b)));
+    return f2_from(r);
+}
+__device__ __forceinline__ float2 mul_f2(float2 a, float2 b)
+{
+    unsigned long long r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(f2_bits(a)), "l"(f2_bits(b)));
+    return f2_from(r);
+}
+__device__ __forceinline__ float2 fma_f2(float2 a, float2 b, float2 c)
+{
+    unsigned long long r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(f2_bits(a)), "l"(f2_bits(b)),
+        "l"(f2_bits(c)));
+    return f2_from(r);
+}
+// a * b = (a.x b.x - a.y b.y, a.x b.y + a.y b.x): the products a.y b are
+// rounded first, then fused into a.x b (as fmaf(a.x, b.x, -(a.y b.y))).
 __device__ __forceinline__ float2 cmul(float2 a, float2 b)
 {
-    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+    const float2 p = mul_f2(make_float2(a.y, a.y), make_float2(b.y, b.x));
+    return fma_f2(make_float2(a.x, a.x), b, make_float2(-p.x, p.y));
 }
-// a * conj(b)
+// a * conj(b) = (a.x b.x + a.y b.y, a.y b.x - a.x b.y)
 __device__ __forceinline__ float2 cmulc(float2 a, float2 b)
 {
-    return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.y, b.x, -a.x * b.y));
+    const float2 p = mul_f2(make_float2(a.y, a.x), make_float2(b.y, b.y));
+    return fma_f2(make_float2(a.x, a.y), make_float2(b.x, b.x), make_float2(p.x, -p.y));
 }
 
 // d * exp(S * 2 pi i j / 16) with j known at compile time after unrolling.
@@ -50,7 +88,9 @@ __device__ __forceinline__ float2 rot16(float2 d, int j)
     if (j == 0) return d;
     if (j == 4) return S < 0 ? make_float2(d.y, -d.x) : make_float2(-d.y, d.x);
     const float c = cos16(j), s = S < 0 ? -sin16(j) : sin16(j);
-    return make_float2(fmaf(d.x, c, -d.y * s), fmaf(d.x, s, d.y * c));
+    // (d.x c - d.y s, d.x s + d.y c)
+    const float2 p = mul_f2(make_float2(d.y, d.y), make_float2(s, c));
+    return fma_f2(make_float2(d.x, d.x), make_float2(c, s), make_float2(-p.x, p.y));
 }
 
 template <int R>

@@ -535,9 +535,13 @@ __global__ void __launch_bounds__(32) spread_es_window_kernel(SpreadArgs a)
 // band zeroed beforehand).  Consecutive samples of a column share their
 // first tap row about 1/(alpha (1 + q)) times, so a row is flushed about
 // alpha times per sample.  Lanes need no step synchronisation.
+constexpr int kDenseAhead = 3;  // rows of u1 and q in flight per lane
+constexpr int kDenseRing = 4;   // ring slots (> kDenseAhead, power of two)
+constexpr int kDenseRingBytes = kDenseRing * 32 * (8 + 4);  // per warp
+
 template <int W, bool TAB = false>
 __device__ __forceinline__ void window_atomic_item(const SpreadArgs& a, int it, int lane,
-                                                   float4* tsm = nullptr)
+                                                   char* ring, float4* tsm = nullptr)
 {
     constexpr int WX = W + kWindowSpare;
     const int ncb = (a.n1x + 31) / 32;
@@ -581,8 +585,24 @@ __device__ __forceinline__ void window_atomic_item(const SpreadArgs& a, int it, 
         for (int i = 0; i < WX; ++i)
             if (lane_on && i < W + maxoff) atomicAdd(row + ((X0 + i) & mx), acc[b][i]);
     };
-    float qn = __ldg(&a.q[(size_t)ny0 * a.n1x + nxc]);
-    float2 un = __ldg(&a.u1[(size_t)ny0 * a.n1x + nxc]);
+    // u1 and q of the run's rows are copied asynchronously (cp.async) into a
+    // per-lane ring of kDenseRing slots in shared memory, kDenseAhead rows
+    // ahead of use
+    float2* ring_u = reinterpret_cast<float2*>(ring);
+    float* ring_q = reinterpret_cast<float*>(ring_u + kDenseRing * 32);
+    auto issue_row = [&](int r) {  // always commits one group (empty past the run)
+        if (r <= nyl) {
+            const size_t n = (size_t)r * a.n1x + nxc;
+            const int slot = (r - ny0) & (kDenseRing - 1);
+            const unsigned du = (unsigned)__cvta_generic_to_shared(ring_u + slot * 32 + lane);
+            const unsigned dq = (unsigned)__cvta_generic_to_shared(ring_q + slot * 32 + lane);
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(du), "l"(a.u1 + n));
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dq), "l"(a.q + n));
+        }
+        asm volatile("cp.async.commit_group;");
+    };
+#pragma unroll
+    for (int r = 0; r < kDenseAhead; ++r) issue_row(ny0 + r);
     int tab_ty = -1;
     const int tcol0 = ((it % ncb) * 32) / kSrcTile;  // first source-tile column of the warp
     // the table float4 this lane stages, loaded one tile row ahead
@@ -597,16 +617,18 @@ __device__ __forceinline__ void window_atomic_item(const SpreadArgs& a, int it, 
     };
     float4 tnext = load_tab(ny0 / kSrcTile);
     for (int ny = ny0; ny <= nyl; ++ny) {
-        const float q = qn;
-        const float2 u = un;
-        if (ny < nyl) {
-            qn = __ldg(&a.q[(size_t)(ny + 1) * a.n1x + nxc]);
-            un = __ldg(&a.u1[(size_t)(ny + 1) * a.n1x + nxc]);
-        }
-        const AxisEntry ey = a.ay[ny];
+        const AxisEntry ey = a.ay[ny];  // the same entry for every lane of the warp
+        const AxisPos py = a.py[ny];
+        // this lane's copy of row ny has landed once at most kDenseAhead - 1
+        // younger groups are pending; then queue row ny + kDenseAhead
+        asm volatile("cp.async.wait_group %0;" ::"n"(kDenseAhead - 1));
+        const int slot = (ny - ny0) & (kDenseRing - 1);
+        const float q = ring_q[slot * 32 + lane];
+        const float2 u = ring_u[slot * 32 + lane];
+        issue_row(ny + kDenseAhead);
         int l0x, l0y;
         float dx, dy;
-        sample_pos(ex, ey, px, a.py[ny], q, a.half_w, l0x, l0y, dx, dy);
+        sample_pos(ex, ey, px, py, q, a.half_w, l0x, l0y, dx, dy);
         const int off = l0x - X0, d = l0y - R0;
         if (live && (off < 0 || off > maxoff || d < 0 || d > 2)) {
 #pragma unroll
@@ -660,8 +682,11 @@ template <int W, bool TAB = false>
 __global__ void __launch_bounds__(128) spread_es_dense_kernel(SpreadArgs a, int items)
 {
     __shared__ float4 tsm[4][TAB ? 8 * W : 1];
+    __shared__ __align__(16) char ring[4][kDenseRingBytes];
     const int it = blockIdx.x * 4 + threadIdx.x / 32;
-    if (it < items) window_atomic_item<W, TAB>(a, it, threadIdx.x % 32, tsm[threadIdx.x / 32]);
+    if (it < items)
+        window_atomic_item<W, TAB>(a, it, threadIdx.x % 32, ring[threadIdx.x / 32],
+                                   tsm[threadIdx.x / 32]);
 }
 
 // Fallback spread of band tile `tile` (kTileX x kTileY) by a whole block:
