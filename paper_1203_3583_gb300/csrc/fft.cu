@@ -20,8 +20,9 @@ namespace asfd {
 
 namespace {
 
+// (4096-point rows: at most 64 registers, four 256-thread blocks per SM)
 template <int L>
-__global__ void __launch_bounds__(RowCfg<L>::THREADS)
+__global__ void __launch_bounds__(RowCfg<L>::THREADS, L == 4096 ? 4 : 1)
 fft_rows_kernel(RowArgs a)
 {
     extern __shared__ float2 sm[];
