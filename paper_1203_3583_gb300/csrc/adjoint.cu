@@ -15,6 +15,8 @@
 // dq/dd1 = z0 / (z0 - d1)^2 = (1 + q)^2 / z0.  These are the exact
 // derivatives of the discrete forward computation, so <A x, y> = <x, A^H y>
 // holds to rounding.
+#include <algorithm>
+
 #include "asfd_impl.cuh"
 #include "sample.cuh"
 
@@ -95,6 +97,131 @@ __global__ void __launch_bounds__(256) interp_grad_kernel(InterpArgs a)
     }
 }
 
+// psi and d psi / dz of the ES kernel for two taps at once (packed FP32x2; the
+// MUFU square root and exponential), 1 - u^2 floored at 1e-12 as in
+// es_weight_deriv_fast.  neg_c2 = -(2/w)^2; d psi/dz = psi z rsqrt(r) beta neg_c2.
+__device__ __forceinline__ void es_weight_deriv2_fast(float2 z, float neg_c2, float beta_log2e,
+                                                      float beta_negc2, float2& psi, float2& dpsi)
+{
+    const float2 t = mul2(z, neg_c2);
+    float2 r = fma2v(t, z, make_float2(1.f, 1.f));
+    r.x = fmaxf(r.x, 1e-12f);
+    r.y = fmaxf(r.y, 1e-12f);
+    float2 rs, e;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(rs.x) : "f"(r.x));
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(rs.y) : "f"(r.y));
+    const float2 s = fma2v(r, rs, make_float2(-1.f, -1.f));
+    const float2 arg = mul2(s, beta_log2e);
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e.x) : "f"(arg.x));
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e.y) : "f"(arg.y));
+    psi = e;
+    const float2 zr = make_float2(z.x * rs.x, z.y * rs.y);
+    dpsi = mul2(make_float2(e.x * zr.x, e.y * zr.y), beta_negc2);
+}
+
+// Interpolation with a register window (widths up to 7): warp item `it` takes
+// 32 consecutive source columns (one per lane) over `rows` consecutive rows.
+// Consecutive samples of a column read nearly the same W x W cells of b~, so
+// each lane keeps them in registers and, when the first tap row moves down by
+// d < W rows, moves the window up and reads only the d new rows; a changed
+// first tap column or a larger jump reloads the window.  Sums, outputs and
+// arithmetic per sample are those of interp_grad_kernel.
+template <int W>
+__global__ void __launch_bounds__(128) interp_window_kernel(InterpArgs a, int rows, int items)
+{
+    const int it = blockIdx.x * 4 + threadIdx.x / 32, lane = threadIdx.x % 32;
+    if (it >= items) return;
+    const int ncb = (a.n1x + 31) / 32;
+    const int nx = (it % ncb) * 32 + lane;
+    const int ny0 = (it / ncb) * rows;
+    const int nyl = min(ny0 + rows, a.n1y) - 1;
+    if (nx >= a.n1x || ny0 > nyl) return;
+    const int mx = a.nfx - 1, my = a.nfy - 1;
+    const float neg_c2 = -a.two_over_w * a.two_over_w;
+    const float beta_negc2 = a.beta * neg_c2;
+    const AxisEntry ex = a.ax[nx];
+    const AxisPos px = a.px[nx];
+
+    float2 v[W][W];
+    int X0 = 0, R0 = 0;
+    bool live = false;
+    auto load_row = [&](int b, int row) {
+        const float2* g = a.grid + (size_t)(row & my) * a.nfx;
+#pragma unroll
+        for (int i = 0; i < W; ++i) v[b][i] = __ldg(&g[(X0 + i) & mx]);
+    };
+    size_t n = (size_t)ny0 * a.n1x + nx;
+    float qn = __ldg(&a.q[n]);
+    float2 un = a.u1 ? __ldg(&a.u1[n]) : make_float2(1.f, 0.f);
+    for (int ny = ny0; ny <= nyl; ++ny, n += a.n1x) {
+        const float q = qn;
+        const float2 u = un;
+        if (ny < nyl) {
+            qn = __ldg(&a.q[n + a.n1x]);
+            if (a.u1) un = __ldg(&a.u1[n + a.n1x]);
+        }
+        const AxisEntry ey = a.ay[ny];
+        int l0x, l0y;
+        float dx, dy;
+        sample_pos(ex, ey, px, a.py[ny], q, a.half_w, l0x, l0y, dx, dy);
+        const int d = l0y - R0;
+        if (!live || l0x != X0 || d < 0 || d >= W) {
+            X0 = l0x;
+            R0 = l0y;
+#pragma unroll
+            for (int b = 0; b < W; ++b) load_row(b, R0 + b);
+            live = true;
+        } else {
+            for (int k = 0; k < d; ++k) {  // slide down one row
+#pragma unroll
+                for (int b = 0; b + 1 < W; ++b)
+#pragma unroll
+                    for (int i = 0; i < W; ++i) v[b][i] = v[b + 1][i];
+                load_row(W - 1, R0 + W + k);
+            }
+            R0 = l0y;
+        }
+        float wx[W], dwx[W], wy[W], dwy[W];
+#pragma unroll
+        for (int i = 0; i < W; ++i) {
+            float2 psi, dpsi;
+            es_weight_deriv2_fast(make_float2(dx + (float)i - a.half_w, dy + (float)i - a.half_w),
+                                  neg_c2, a.beta_log2e, beta_negc2, psi, dpsi);
+            wx[i] = psi.x;
+            dwx[i] = dpsi.x;
+            wy[i] = psi.y;
+            dwy[i] = dpsi.y;
+        }
+        float2 i0 = make_float2(0.f, 0.f), ixs = i0, iys = i0;
+#pragma unroll
+        for (int b = 0; b < W; ++b) {
+            float2 s0 = make_float2(0.f, 0.f), sd = s0;
+#pragma unroll
+            for (int i = 0; i < W; ++i) {
+                s0 = fma2(v[b][i], wx[i], s0);
+                sd = fma2(v[b][i], dwx[i], sd);
+            }
+            i0 = fma2(s0, wy[b], i0);
+            ixs = fma2(sd, wy[b], ixs);
+            iys = fma2(s0, dwy[b], iys);
+        }
+        // E = c / u1 (unit modulus prefactor)
+        const float2 E = sample_value_fast(make_float2(1.f, 0.f), ex, ey, q);
+        if (a.gu1) a.gu1[n] = make_float2(E.x * i0.x + E.y * i0.y, E.x * i0.y - E.y * i0.x);
+        if (a.gd1) {
+            const float2 c = make_float2(u.x * E.x - u.y * E.y, u.x * E.y + u.y * E.x);
+            const float opq = 1.0f + q;
+            const float k2 = opq * opq * a.inv_z0;
+            const float dtheta = 3.14159265358979f * (ex.a + ey.a) * k2;
+            const float gx = ex.s * k2, gy = ey.s * k2;
+            const float im_c_i0 = c.y * i0.x - c.x * i0.y;
+            const float re_c_ix = c.x * ixs.x + c.y * ixs.y;
+            const float re_c_iy = c.x * iys.x + c.y * iys.y;
+            a.gd1[n] = -dtheta * im_c_i0 - gx * re_c_ix - gy * re_c_iy;
+        }
+    }
+}
+
 }  // namespace
 
 asfd_status launch_interp_grad(asfd_plan_s* P, const float2* u1, float2* gu1, float* gd1,
@@ -122,6 +249,22 @@ asfd_status launch_interp_grad(asfd_plan_s* P, const float2* u1, float2* gu1, fl
     const size_t n = (size_t)P->prm.n1x * P->prm.n1y;
     const unsigned blocks = (unsigned)((n + 255) / 256);
     cudaError_t e = cudaSuccess;
+    if (P->w <= kMaxWindowWidth) {
+        // warp items of 32 columns x `rows` rows, about 2400 of them
+        const long long ncb = (P->prm.n1x + 31) / 32;
+        const int rows = (int)std::max<long long>(
+            8, std::min<long long>(256, (long long)P->prm.n1y * ncb / 2432));
+        const int items = (int)(ncb * ((P->prm.n1y + rows - 1) / rows));
+        switch (P->w) {
+#define ASFD_IWW(W) case W: interp_window_kernel<W><<<(items + 3) / 4, 128, 0, st>>>(a, rows, items); break;
+            ASFD_IWW(2) ASFD_IWW(3) ASFD_IWW(4) ASFD_IWW(5) ASFD_IWW(6) ASFD_IWW(7)
+#undef ASFD_IWW
+            default: break;
+        }
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(e, "interp_window_kernel launch");
+        return ASFD_OK;
+    }
     switch (P->w) {
 #define ASFD_IW(W) case W: interp_grad_kernel<W><<<blocks, 256, 0, st>>>(a); break;
         ASFD_IW(2) ASFD_IW(3) ASFD_IW(4) ASFD_IW(5) ASFD_IW(6) ASFD_IW(7) ASFD_IW(8) ASFD_IW(9)

@@ -564,46 +564,30 @@ asfd_status plan_build_colored(asfd_plan_s* P, bool wraps, cudaStream_t st)
 {
     const asfd_params& p = P->prm;
     P->colored = false;
-    col_range_kernel<<<(p.n1x + 127) / 128, 128, 0, st>>>(P->q, P->ax, P->bux, p.n1x, p.n1y,
-                                                           P->col_range);
-    row_range_kernel<<<p.n1y, 256, 0, st>>>(P->q, P->ay, P->buy, p.n1x, P->row_range);
+    P->windowed = false;
+    P->dense = false;
     min_step_kernel<<<kStepBlocks, 256, 0, st>>>(P->q, P->ax, P->ay, P->bux, P->buy, p.n1x, p.n1y,
                                                  P->step_min);
     ASFD_CUDA(cudaGetLastError());
-    std::vector<double> cr(2 * (size_t)p.n1x), rr(2 * (size_t)p.n1y);
     std::vector<float> sm(2 * kStepBlocks);
-    ASFD_CUDA(cudaMemcpyAsync(cr.data(), P->col_range, sizeof(double) * cr.size(),
-                              cudaMemcpyDeviceToHost, st));
-    ASFD_CUDA(cudaMemcpyAsync(rr.data(), P->row_range, sizeof(double) * rr.size(),
-                              cudaMemcpyDeviceToHost, st));
     ASFD_CUDA(cudaMemcpyAsync(sm.data(), P->step_min, sizeof(float) * sm.size(),
                               cudaMemcpyDeviceToHost, st));
     ASFD_CUDA(cudaStreamSynchronize(st));
-    double msx = 3e38, msy = 3e38, spread_y = 0.0;
+    double msx = 3e38, msy = 3e38;
     for (int b = 0; b < kStepBlocks; ++b) {
         msx = std::min(msx, (double)sm[2 * b]);
         msy = std::min(msy, (double)sm[2 * b + 1]);
     }
-    for (int ny = 0; ny < p.n1y; ++ny) spread_y = std::max(spread_y, rr[2 * ny + 1] - rr[2 * ny]);
-    double spread_x = 0.0;
-    for (int nx = 0; nx < p.n1x; ++nx) spread_x = std::max(spread_x, cr[2 * nx + 1] - cr[2 * nx]);
-    P->col_spread_x = spread_x;
-    P->windowed = false;
-    P->dense = false;
     if (p.n1x < 2) msx = 1e30;
     if (p.n1y < 2) msy = 1e30;
     P->min_step_x = msx;
     P->min_step_y = msy;
-    P->row_spread_y = spread_y;
-    const double margin = 0.01;
+    P->row_spread_y = 0.0;
+    P->col_spread_x = 0.0;
     // the minimum spacing must clear FP32 rounding of the coordinates (~1e-6
-    // cells) so that the first tap column is non-decreasing along a row
-    if (wraps || !(msx > 1e-3) || !(msy > 1e-3) || P->w > kMaxRingWidth) return ASFD_OK;
-    const double sxd = std::ceil((P->w + margin) / msx);
-    const double hd = std::ceil((P->w + spread_y + margin) / msy);
-    // the register-window kernels also need columns w apart across rows
-    const double sxw = std::ceil((P->w + spread_x + margin) / msx);
-    if (P->w <= kMaxWindowWidth && !p.deterministic) {
+    // cells) so that the first tap rows and columns are non-decreasing
+    const bool monotone = !wraps && msx > 1e-3 && msy > 1e-3;
+    if (monotone && P->w <= kMaxWindowWidth && !p.deterministic) {
         // register windows flushed to the fine grid with float atomics (the
         // fastest path, and the only efficient one for dense maps); runs of
         // dense_rows rows per lane, enough warp items to fill the GPU
@@ -614,6 +598,29 @@ asfd_status plan_build_colored(asfd_plan_s* P, bool wraps, cudaStream_t st)
         P->dense = true;
         return ASFD_OK;
     }
+    if (!monotone || P->w > kMaxRingWidth) return ASFD_OK;
+
+    // atomic-free tiles: row and column extents of the samples' coordinates
+    col_range_kernel<<<(p.n1x + 127) / 128, 128, 0, st>>>(P->q, P->ax, P->bux, p.n1x, p.n1y,
+                                                           P->col_range);
+    row_range_kernel<<<p.n1y, 256, 0, st>>>(P->q, P->ay, P->buy, p.n1x, P->row_range);
+    ASFD_CUDA(cudaGetLastError());
+    std::vector<double> cr(2 * (size_t)p.n1x), rr(2 * (size_t)p.n1y);
+    ASFD_CUDA(cudaMemcpyAsync(cr.data(), P->col_range, sizeof(double) * cr.size(),
+                              cudaMemcpyDeviceToHost, st));
+    ASFD_CUDA(cudaMemcpyAsync(rr.data(), P->row_range, sizeof(double) * rr.size(),
+                              cudaMemcpyDeviceToHost, st));
+    ASFD_CUDA(cudaStreamSynchronize(st));
+    double spread_y = 0.0, spread_x = 0.0;
+    for (int ny = 0; ny < p.n1y; ++ny) spread_y = std::max(spread_y, rr[2 * ny + 1] - rr[2 * ny]);
+    for (int nx = 0; nx < p.n1x; ++nx) spread_x = std::max(spread_x, cr[2 * nx + 1] - cr[2 * nx]);
+    P->row_spread_y = spread_y;
+    P->col_spread_x = spread_x;
+    const double margin = 0.01;
+    const double sxd = std::ceil((P->w + margin) / msx);
+    const double hd = std::ceil((P->w + spread_y + margin) / msy);
+    // the register-window tiles also need columns w apart across rows
+    const double sxw = std::ceil((P->w + spread_x + margin) / msx);
     // beyond 64 samples between lanes (samples packed far below one cell
     // apart) few lanes find work in a tile and the atomic kernel is faster
     if (!(sxd <= 64.0) || !(hd <= 64.0)) return ASFD_OK;
