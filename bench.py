@@ -173,6 +173,10 @@ SPREAD_KERNEL = {0: "spread_es_colored_kernel", 1: "spread_es_atomic_kernel",
 # u1 + d1 (12) + fine-grid write (4 M^2 8 / N^2 = 32) + row read (32) + row write
 # (16) + column read (16) + u2 write (8), sigma = 2 and N = M
 STEP_BYTES_PER_SAMPLE = 116
+# DRAM bytes (read + write) per launch of the dominant kernel from one ncu capture
+# of the current kernel (profiles/spread_es_dense_w7_smooth_random2048.md); a
+# kernel or workload without a capture of its current code reports null
+NCU_TRAFFIC = {("spread_es_dense_kernel<7>", "smooth_random2048"): 86.793984e6 + 1.880576e6}
 
 
 def oracle_sample(g, u1, d1, seconds, seed=7):
@@ -307,7 +311,8 @@ def run_ours(args):
     achieved = sb[dom] / (mean_stage[dom] * 1e-3) / 1e9
     names = [f"{SPREAD_KERNEL[info['spread_kind']]}<{args.width}>"] + STAGE_KERNELS[1:]
     roofline = {"bound": "hbm", "kernel": names[dom], "achieved": achieved, "peak": peak,
-                "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                "unit": "GB/s", "frac": achieved / peak,
+                "traffic": NCU_TRAFFIC.get((names[dom], args.workload)),
                 "algorithmic_bytes_per_launch": sb[dom], "peak_source": peak_src,
                 "stage_ms": {k: v for k, v in zip(names, mean_stage)},
                 "stage_frac": {k: b / (t * 1e-3) / 1e9 / peak
