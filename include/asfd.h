@@ -204,7 +204,7 @@ asfd_status asfd_learned_set_params(asfd_plan plan, const float* params_host, si
  * One Adam step (learning rate lr) on the relative squared error
  * |u2 - ref|^2 / |ref|^2 of the forward transform of u1_dev against
  * ref_u2_dev (device [m2y][m2x] complex, e.g. the ES-kernel transform at a
- * large width, the judge of the learned kernel's error).  Runs the forward,
+ * large width, the reference for the learned kernel's error).  Runs the forward,
  * the loss gradient, the adjoint FFT passes, the table, deconvolution and MLP
  * gradients and the update on `stream`.  If loss_host is not NULL the loss
  * before the update is written there (synchronises `stream`).

@@ -6,7 +6,7 @@ plan of kind "learned" and is trained on the GPU by asfd_learned_train_step,
 whose forward, adjoint, gradient and optimiser kernels are the library's
 own.  Training pairs are seeded (surface, field) inputs of one geometry; the
 target of each pair is the transform with the ES kernel at width 12, the
-judge of the learned kernel's error.
+reference for the learned kernel's error.
 
     model = train_model(train_set(...), steps=400)
     model.save("learned_w4.npz"); LearnedModel.load(path).apply_to(plan)
