@@ -66,6 +66,10 @@ def bind(path: str):
     lib.asfd_oracle_eq7.argtypes = [ctypes.POINTER(Geom), dp, dp, ctypes.c_int,
                                     ip, ip, dp, ctypes.c_int]
     lib.asfd_oracle_eq7.restype = ctypes.c_int
+    for name in ("asfd_oracle_eq5", "asfd_oracle_eq2"):
+        fn = getattr(lib, name)
+        fn.argtypes = lib.asfd_oracle_eq7.argtypes
+        fn.restype = ctypes.c_int
     lib.asfd_oracle_eq7_grad.argtypes = [ctypes.POINTER(Geom), dp, dp, ctypes.c_int,
                                          ip, ip, dp, dp, dp, ctypes.c_int]
     lib.asfd_oracle_eq7_grad.restype = ctypes.c_int
@@ -136,6 +140,36 @@ def eq7(g: dict, u1: np.ndarray, d1: np.ndarray, points=None, nthreads: int = 0,
     if points is None:
         return out.reshape(gg.m2y, gg.m2x)
     return out
+
+
+def _direct(name: str, g: dict, u1, d1, points, nthreads, lib):
+    gg = _geom(g)
+    u1c = np.ascontiguousarray(u1, np.complex128)
+    d1c = np.ascontiguousarray(d1, np.float64)
+    if u1c.shape != (gg.n1y, gg.n1x) or d1c.shape != (gg.n1y, gg.n1x):
+        raise ValueError("u1 and d1 must have shape (n1y, n1x)")
+    mx, my = _points(g, points)
+    out = np.empty(mx.size, np.complex128)
+    rc = getattr(lib or _load(), name)(ctypes.byref(gg), _dptr(u1c.view(np.float64)), _dptr(d1c),
+                                       int(mx.size), _iptr(mx), _iptr(my),
+                                       _dptr(out.view(np.float64)), int(nthreads))
+    if rc != 0:
+        raise RuntimeError(f"{name} rejected its arguments")
+    return out.reshape(gg.m2y, gg.m2x) if points is None else out
+
+
+def eq5(g: dict, u1: np.ndarray, d1: np.ndarray, points=None, nthreads: int = 0,
+        lib=None) -> np.ndarray:
+    """Eq. 5 (per-sample r0 in the destination chirp) at destination points;
+    arguments and result as for eq7."""
+    return _direct("asfd_oracle_eq5", g, u1, d1, points, nthreads, lib)
+
+
+def eq2(g: dict, u1: np.ndarray, d1: np.ndarray, points=None, nthreads: int = 0,
+        lib=None) -> np.ndarray:
+    """Eq. 2 (Huygens sum with the exact distance of Eq. 3) at destination
+    points; arguments and result as for eq7."""
+    return _direct("asfd_oracle_eq2", g, u1, d1, points, nthreads, lib)
 
 
 def eq7_grad(g: dict, u1: np.ndarray, d1: np.ndarray, gu2: np.ndarray, points=None,

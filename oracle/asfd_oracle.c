@@ -31,6 +31,10 @@
  *  - arrays are row-major [y][x], x fastest; complex values are interleaved
  *    (re, im) FP64 pairs.
  *
+ * Also Eq. 5 (asfd_oracle_eq5: the destination chirp with r0 per sample) and
+ * Eq. 2 (asfd_oracle_eq2: the exact distance of Eq. 3, no Fresnel
+ * approximation), for measuring the approximations of Eqs. 4 and 6.
+ *
  * Pins (tests/test_oracle_pins.py): single-sample closed form, d1 = 0 at the
  * natural pitch against numpy's FFT, d1 = const against two dense DFT matmuls
  * and against planar single-FFT Fresnel propagation over z0 - c, terraced
@@ -133,6 +137,111 @@ int asfd_oracle_eq7(const asfd_oracle_geom* g, const double* u1, const double* d
         outer_factor(g, x2x, x2y, &o_re, &o_im);
         out[2 * i] = o_re * acc_re - o_im * acc_im;
         out[2 * i + 1] = o_re * acc_im + o_im * acc_re;
+    }
+    return 0;
+}
+
+/*
+ * Eq. 5 (Fresnel diffraction from the arbitrary surface before the
+ * destination-chirp approximation of Eq. 6) at npts destination points:
+ *
+ *   u(x2) = exp(ik z0) / (i lambda z0)
+ *           * sum_n p1x p1y u_I(n) u1(n) exp(ik(-d1 + |x1|^2/(2 r0)))
+ *                   exp(-ik x1.x2 / r0) exp(ik |x2|^2 / (2 r0)),
+ *
+ * with r0 = z0 - d1(n) in all three exponentials.  The last exponential is
+ * printed without "ik" in the paper; it is read as exp(ik|x2|^2/(2 r0)), the
+ * term of Eq. 4 it comes from.  Arguments as for asfd_oracle_eq7.
+ */
+int asfd_oracle_eq5(const asfd_oracle_geom* g, const double* u1, const double* d1,
+                    int npts, const int* mx, const int* my, double* out, int nthreads)
+{
+    if (!g || !u1 || !d1 || !mx || !my || !out || npts < 0) return -1;
+    const double k = 2.0 * ORACLE_PI / g->lambda;
+    const double w = g->p1x * g->p1y;
+    set_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int i = 0; i < npts; ++i) {
+        const double x2x = (mx[i] - g->m2x / 2) * g->p2x;
+        const double x2y = (my[i] - g->m2y / 2) * g->p2y;
+        const double x2sq = x2x * x2x + x2y * x2y;
+        double acc_re = 0.0, acc_im = 0.0;
+        for (int ny = 0; ny < g->n1y; ++ny) {
+            const double x1y = (ny - g->n1y / 2) * g->p1y;
+            double row_re = 0.0, row_im = 0.0;
+            for (int nx = 0; nx < g->n1x; ++nx) {
+                const size_t n = (size_t)ny * g->n1x + nx;
+                const double x1x = (nx - g->n1x / 2) * g->p1x;
+                const double h = d1[n];
+                const double r0 = g->z0 - h;
+                const double ph_inc = k * h;  /* u_I = exp(ik d1) */
+                const double ph_src = k * (-h + (x1x * x1x + x1y * x1y) / (2.0 * r0));
+                const double ph_x = -k * (x1x * x2x + x1y * x2y) / r0;
+                const double ph_dst = k * x2sq / (2.0 * r0);
+                const double ph = ph_inc + ph_src + ph_x + ph_dst;
+                const double c = cos(ph), s = sin(ph);
+                const double ur = u1[2 * n], ui = u1[2 * n + 1];
+                row_re += ur * c - ui * s;
+                row_im += ur * s + ui * c;
+            }
+            acc_re += row_re;
+            acc_im += row_im;
+        }
+        acc_re *= w;
+        acc_im *= w;
+        /* exp(ik z0) / (i lambda z0) */
+        const double a = g->lambda * g->z0, ph0 = k * g->z0;
+        const double o_re = sin(ph0) / a, o_im = -cos(ph0) / a;
+        out[2 * i] = o_re * acc_re - o_im * acc_im;
+        out[2 * i + 1] = o_re * acc_im + o_im * acc_re;
+    }
+    return 0;
+}
+
+/*
+ * Eq. 2 (Huygens diffraction from the arbitrary surface, no Fresnel
+ * approximation) at npts destination points:
+ *
+ *   u(x2) = z0 / (i lambda) * sum_n p1x p1y u_I(n) u1(n) exp(ik r) / r^2,
+ *   r = sqrt(|x2 - x1|^2 + (z0 - d1)^2)                       (Eq. 3),
+ *
+ * with u_I = exp(ik d1).  Arguments as for asfd_oracle_eq7.
+ */
+int asfd_oracle_eq2(const asfd_oracle_geom* g, const double* u1, const double* d1,
+                    int npts, const int* mx, const int* my, double* out, int nthreads)
+{
+    if (!g || !u1 || !d1 || !mx || !my || !out || npts < 0) return -1;
+    const double k = 2.0 * ORACLE_PI / g->lambda;
+    const double w = g->p1x * g->p1y;
+    set_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int i = 0; i < npts; ++i) {
+        const double x2x = (mx[i] - g->m2x / 2) * g->p2x;
+        const double x2y = (my[i] - g->m2y / 2) * g->p2y;
+        double acc_re = 0.0, acc_im = 0.0;
+        for (int ny = 0; ny < g->n1y; ++ny) {
+            const double x1y = (ny - g->n1y / 2) * g->p1y;
+            double row_re = 0.0, row_im = 0.0;
+            for (int nx = 0; nx < g->n1x; ++nx) {
+                const size_t n = (size_t)ny * g->n1x + nx;
+                const double x1x = (nx - g->n1x / 2) * g->p1x;
+                const double h = d1[n];
+                const double dx = x2x - x1x, dy = x2y - x1y, dz = g->z0 - h;
+                const double r2 = dx * dx + dy * dy + dz * dz;
+                const double r = sqrt(r2);
+                const double ph = k * h + k * r;
+                const double c = cos(ph) / r2, s = sin(ph) / r2;
+                const double ur = u1[2 * n], ui = u1[2 * n + 1];
+                row_re += ur * c - ui * s;
+                row_im += ur * s + ui * c;
+            }
+            acc_re += row_re;
+            acc_im += row_im;
+        }
+        /* z0 / (i lambda) = -i z0 / lambda */
+        const double f = w * g->z0 / g->lambda;
+        out[2 * i] = f * acc_im;
+        out[2 * i + 1] = -f * acc_re;
     }
     return 0;
 }

@@ -160,3 +160,73 @@ ALL_PINS = {
     "terraces": (pin_terraces, 1e-9),
     "single_sample_modulus": (pin_single_sample_modulus, 1e-12),
 }
+
+
+# --- Eq. 5 and Eq. 2 (direct sums before the approximations of Eqs. 4 and 6) ---------
+
+def pin_eq5_equals_eq7_flat(eq5, eq2, eq7, n1x=20, n1y=14, p1x=10e-6, p1y=8e-6, lam=633e-9,
+                            z0=0.05, seed=31):
+    """d1 = 0: r0 = z0 everywhere, so Eq. 6 is exact and Eq. 5 is Eq. 7."""
+    rng = np.random.default_rng(seed)
+    u1 = _rng_field(rng, (n1y, n1x)).astype(np.complex128)
+    g = dict(n1x=n1x, n1y=n1y, p1x=p1x, p1y=p1y, m2x=16, m2y=18, p2x=12e-6, p2y=9e-6,
+             lam=lam, z0=z0)
+    d1 = np.zeros((n1y, n1x))
+    return rel_l2(eq5(g, u1, d1), eq7(g, u1, d1))
+
+
+def pin_eq5_planar_shift(eq5, eq2, eq7, c=0.4e-3, n1x=18, n1y=16, p1x=10e-6, p1y=7e-6,
+                         lam=532e-9, z0=0.04, seed=32):
+    """d1 = c: the exponentials of Eq. 5 combine to exp(ik|x1 - x2|^2/(2 (z0 - c)))
+    (u_I and exp(-ik d1) cancel), i.e. planar Fresnel propagation over z0 - c
+    with the prefactor exp(ik z0)/(i lambda z0) instead of
+    exp(ik(z0 - c))/(i lambda (z0 - c)); planar propagation is Eq. 7 at d1 = 0."""
+    rng = np.random.default_rng(seed)
+    u1 = _rng_field(rng, (n1y, n1x)).astype(np.complex128)
+    g = dict(n1x=n1x, n1y=n1y, p1x=p1x, p1y=p1y, m2x=14, m2y=20, p2x=11e-6, p2y=13e-6,
+             lam=lam, z0=z0)
+    r0 = z0 - c
+    gz = dict(g, z0=r0)
+    k = 2 * np.pi / lam
+    ref = eq7(gz, u1, np.zeros((n1y, n1x))) * (r0 / z0) * np.exp(1j * k * c)
+    return rel_l2(eq5(g, u1, np.full((n1y, n1x), c)), ref)
+
+
+def pin_eq2_depth_shift(eq5, eq2, eq7, c=0.3e-3, n1x=16, n1y=14, p1x=10e-6, p1y=9e-6,
+                        lam=633e-9, z0=0.05, seed=33):
+    """d1 = c: Eq. 2 depends on the surface only through u_I = exp(ikc) and the
+    distance z0 - c, so it equals z0/(z0 - c) exp(ikc) times Eq. 2 of the flat
+    surface at distance z0 - c."""
+    rng = np.random.default_rng(seed)
+    u1 = _rng_field(rng, (n1y, n1x)).astype(np.complex128)
+    g = dict(n1x=n1x, n1y=n1y, p1x=p1x, p1y=p1y, m2x=12, m2y=10, p2x=15e-6, p2y=14e-6,
+             lam=lam, z0=z0)
+    k = 2 * np.pi / lam
+    ref = eq2(dict(g, z0=z0 - c), u1, np.zeros((n1y, n1x))) * (z0 / (z0 - c)) * np.exp(1j * k * c)
+    return rel_l2(eq2(g, u1, np.full((n1y, n1x), c)), ref)
+
+
+def pin_eq2_fresnel_limit(eq5, eq2, eq7, n1=16, p1=20e-6, lam=633e-9, seed=34):
+    """Eq. 2 -> Eq. 5 as the distance grows: the largest neglected term is the
+    amplitude of r^2 ~ z0^2, a relative 2 d1/z0 for a surface of height d1
+    (here +-20 um), then the Fresnel expansion's (Eq. 4) 1/z0^2 and 1/z0^3
+    terms, so doubling z0 must cut the difference at least 1.8-fold, and at
+    z0 = 1 m over this 0.3 mm aperture it is below 1e-5.  Returns the largest of
+    the three measurements over its bound (pass: < 1)."""
+    rng = np.random.default_rng(seed)
+    u1 = _rng_field(rng, (n1, n1)).astype(np.complex128)
+    d1 = rng.uniform(-20e-6, 20e-6, (n1, n1))
+    errs = []
+    for z0 in (0.25, 0.5, 1.0):
+        g = dict(n1x=n1, n1y=n1, p1x=p1, p1y=p1, m2x=12, m2y=12, p2x=25e-6, p2y=25e-6,
+                 lam=lam, z0=z0)
+        errs.append(rel_l2(eq2(g, u1, d1), eq5(g, u1, d1)))
+    return max(errs[1] / errs[0] * 1.8, errs[2] / errs[1] * 1.8, errs[2] / 1e-5)
+
+
+DIRECT_PINS = {
+    "eq5_equals_eq7_flat": (pin_eq5_equals_eq7_flat, 1e-9),
+    "eq5_planar_shift": (pin_eq5_planar_shift, 1e-9),
+    "eq2_depth_shift": (pin_eq2_depth_shift, 1e-9),
+    "eq2_fresnel_limit": (pin_eq2_fresnel_limit, 1.0),
+}

@@ -185,3 +185,53 @@ def test_planted_mistake_fails_a_pin(name, tmp_path):
         if not err < tol:
             failures.append(pname)
     assert failures, f"mutant {name} passed every pin"
+
+
+# --- Eq. 5 and Eq. 2 --------------------------------------------------------------
+
+def _direct_fns(lib=None):
+    def eq5(g, u1, d1, points=None):
+        return oracle.eq5(g, u1, d1, points=points, lib=lib)
+
+    def eq2(g, u1, d1, points=None):
+        return oracle.eq2(g, u1, d1, points=points, lib=lib)
+
+    def eq7(g, u1, d1, points=None):
+        return oracle.eq7(g, u1, d1, points=points, lib=lib)
+    return eq5, eq2, eq7
+
+
+@pytest.mark.parametrize("name", sorted(pins.DIRECT_PINS))
+def test_direct_pin(name):
+    fn, tol = pins.DIRECT_PINS[name]
+    err = fn(*_direct_fns())
+    assert err < tol, f"{name}: {err:.3e} >= {tol:.1e}"
+
+
+DIRECT_MUTANTS = {
+    "eq5_dest_chirp_z0": ("const double ph_dst = k * x2sq / (2.0 * r0);",
+                          "const double ph_dst = k * x2sq / (2.0 * g->z0);"),
+    "eq5_drop_dest_chirp": ("const double ph = ph_inc + ph_src + ph_x + ph_dst;",
+                            "const double ph = ph_inc + ph_src + ph_x;"),
+    "eq5_drop_incident": ("const double ph = ph_inc + ph_src + ph_x + ph_dst;",
+                          "const double ph = ph_src + ph_x + ph_dst;"),
+    "eq2_distance_z0": ("const double dx = x2x - x1x, dy = x2y - x1y, dz = g->z0 - h;",
+                        "const double dx = x2x - x1x, dy = x2y - x1y, dz = g->z0;"),
+    "eq2_phase_sign": ("const double ph = k * h + k * r;", "const double ph = k * h - k * r;"),
+    "eq2_drop_incident": ("const double ph = k * h + k * r;", "const double ph = k * r;"),
+    "eq2_prefactor_sign": ("out[2 * i] = f * acc_im;\n        out[2 * i + 1] = -f * acc_re;",
+                           "out[2 * i] = -f * acc_im;\n        out[2 * i + 1] = f * acc_re;"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(DIRECT_MUTANTS))
+def test_planted_mistake_in_direct_sums_fails_a_pin(name, tmp_path):
+    src = open(os.path.join(os.path.dirname(oracle.__file__), "asfd_oracle.c")).read()
+    old, new = DIRECT_MUTANTS[name]
+    assert src.count(old) == 1, f"mutation anchor for {name} not unique"
+    cpath = tmp_path / "mutant.c"
+    cpath.write_text(src.replace(old, new, 1))
+    lib = oracle.bind(oracle.compile_c(str(cpath), str(tmp_path / "libmutant.so")))
+    failures = [p for p, (fn, tol) in pins.DIRECT_PINS.items()
+                if not fn(*_direct_fns(lib)) < tol]
+    assert failures, f"mutant {name} passed every pin"
