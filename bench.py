@@ -458,6 +458,36 @@ def extra_measurements(args, g, u1, d1, pts, ref_pts, flush, stream):
                      "pairs": len(pairs), "geometry": "smooth_random2048 at 512^2",
                      "final_train_rel_l2": float(np.sqrt(losses[-1]))}}
 
+    # direct sums of Eq. 7, Eq. 5 and Eq. 2 on sampled points: what the
+    # approximations of Eqs. 4 and 6 cost at this size, and the GPU pair rate
+    from paper_1203_3583_gb300.fresnel import direct_sum
+    pts_d = W.sample_points(g, 512, seed=11)
+    vals, dms = {}, {}
+    for form in (7, 5, 2):
+        direct_sum(g, d1, u1_d, form, pts_d)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        v = direct_sum(g, d1, u1_d, form, pts_d)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        dms[form] = e0.elapsed_time(e1)
+        vals[form] = v.cpu().numpy().astype(np.complex128)
+    with FresnelPlan(g, d1, kernel_width=args.width) as p:
+        nu = p.execute(u1_d).cpu().numpy()[pts_d[1], pts_d[0]].astype(np.complex128)
+
+    def rl(a, b):
+        return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+    npairs = n_src * len(pts_d[0])
+    res["direct_sum"] = {
+        "points": len(pts_d[0]),
+        "ms": {f"eq{f}": dms[f] for f in dms},
+        "pairs_per_s": {f"eq{f}": npairs / (dms[f] * 1e-3) for f in dms},
+        "rel_l2": {"nufft_vs_eq7": rl(nu, vals[7]), "eq7_vs_eq5 (Eq. 6)": rl(vals[7], vals[5]),
+                   "eq5_vs_eq2 (Eq. 4, r^2 ~ z0^2)": rl(vals[5], vals[2]),
+                   "nufft_vs_eq2": rl(nu, vals[2])}}
+
     ga, ua, da = W.make("tilt_bump4096")
     with FresnelPlan(ga, da) as p:
         ua_d = torch.as_tensor(ua, device="cuda")

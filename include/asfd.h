@@ -297,6 +297,29 @@ const char* asfd_status_string(asfd_status s);
 const char* asfd_last_error(void);
 
 /*
+ * Direct (O(N^2 M^2)) evaluation of the diffraction sums at npts destination
+ * points, on the GPU, for measuring the paper's approximations and as a fast
+ * reference on sampled points:
+ *   form 7: Eq. 7, the Fourier form that asfd_execute evaluates by NUFFT;
+ *   form 5: Eq. 5, with r0 = z0 - d1 per sample in the destination chirp
+ *           (before the approximation of Eq. 6);
+ *   form 2: Eq. 2, the Huygens sum z0/(i lambda) sum u_I u1 exp(ik r)/r^2 with
+ *           the exact distance r of Eq. 3 (before the Fresnel expansion of
+ *           Eq. 4), u_I = exp(ik d1).
+ * All three use the source weight p1x p1y and the centred coordinates of
+ * asfd_execute.  p: the geometry fields are used (n1x..z0; the spreading fields
+ * are ignored).  d1_dev: device [n1y][n1x] FP64 metres; u1_dev: device
+ * [n1y][n1x] complex; mx_dev, my_dev: device int[npts] destination indices;
+ * out_dev: device complex[npts].  Phases are formed in FP64 per (sample,
+ * point) pair and reduced modulo 2 pi exactly before an FP32 sine/cosine; sums
+ * are FP64.  Allocates (stream-ordered) 32 bytes per source sample for the
+ * duration of the call.  Asynchronous on `stream`.  Errors: ASFD_ERR_ARG.
+ */
+asfd_status asfd_direct_sum(const asfd_params* p, const double* d1_dev, const float* u1_dev,
+                            int form, int npts, const int* mx_dev, const int* my_dev,
+                            float* out_dev, void* stream);
+
+/*
  * Stand-alone batched FFT of the library (the Stockham kernel used by the
  * transform), exposed for unit tests and timing.  in_dev/out_dev: device
  * [lines][n] complex (may alias); n a power of two in [16, 16384];

@@ -98,6 +98,7 @@ SIGNATURES = {
     "asfd_status_string": (ctypes.c_char_p, [_int]),
     "asfd_last_error": (ctypes.c_char_p, []),
     "asfd_fft_lines": (_int, [_int, _int, _int, _vp, _vp, _vp]),
+    "asfd_direct_sum": (_int, [ctypes.POINTER(Params), _vp, _vp, _int, _int, _vp, _vp, _vp, _vp]),
     "asfd_fft_lines_noalloc": (_int, [_int, _int, _int, _vp, _vp, _vp]),
     "asfd_learned_param_count": (ctypes.c_size_t, []),
     "asfd_learned_get_params": (_int, [_vp, _vp, ctypes.c_size_t]),
@@ -283,6 +284,23 @@ def asfd_check_device_status(plan, stream=None) -> None:
 
 def asfd_destroy(plan) -> None:
     _check(load().asfd_destroy(plan))
+
+
+def asfd_direct_sum(params: Params, d1: torch.Tensor, u1: torch.Tensor, form: int,
+                    mx: torch.Tensor, my: torch.Tensor, out: torch.Tensor | None = None,
+                    stream=None) -> torch.Tensor:
+    """Direct GPU sum of Eq. 2, 5 or 7 (form) at the destination points (mx, my)."""
+    npts = int(mx.numel())
+    if my.numel() != npts:
+        raise ValueError("mx and my must have the same length")
+    if out is None:
+        out = torch.empty(npts, dtype=torch.complex64, device=u1.device)
+    _check(load().asfd_direct_sum(
+        ctypes.byref(params), _dev_ptr(d1, torch.float64, (params.n1y, params.n1x), "d1"),
+        _dev_ptr(u1, torch.complex64, (params.n1y, params.n1x), "u1"), int(form), npts,
+        _dev_ptr(mx, torch.int32, (npts,), "mx"), _dev_ptr(my, torch.int32, (npts,), "my"),
+        _dev_ptr(out, torch.complex64, (npts,), "out"), _stream(stream)))
+    return out
 
 
 def asfd_fft_lines(x: torch.Tensor, sign: int = -1, out: torch.Tensor | None = None,

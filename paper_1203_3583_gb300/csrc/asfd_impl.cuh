@@ -174,6 +174,8 @@ asfd_status launch_interp_grad(asfd_plan_s* P, const float2* u1, float2* gu1, fl
 
 // plan helpers
 asfd_status plan_validate(const asfd_params* p, int* nfx, int* nfy, double* beta);
+asfd_status direct_sum(const asfd_params* p, const double* d1, const float2* u1, int form,
+                       int npts, const int* mx, const int* my, float2* out, cudaStream_t st);
 asfd_status plan_alloc(asfd_plan_s* P);
 asfd_status build_twiddles(float2* tw, int L, cudaStream_t st);
 asfd_status plan_build_tables(asfd_plan_s* P, cudaStream_t st);

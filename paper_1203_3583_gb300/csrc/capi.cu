@@ -333,6 +333,15 @@ asfd_status asfd_learned_gradient(asfd_plan P, const float* u1_dev, const float*
     });
 }
 
+asfd_status asfd_direct_sum(const asfd_params* p, const double* d1_dev, const float* u1_dev,
+                            int form, int npts, const int* mx_dev, const int* my_dev,
+                            float* out_dev, void* stream)
+{
+    clear_error();
+    return direct_sum(p, d1_dev, reinterpret_cast<const float2*>(u1_dev), form, npts, mx_dev,
+                      my_dev, reinterpret_cast<float2*>(out_dev), static_cast<cudaStream_t>(stream));
+}
+
 asfd_status asfd_fft_lines(int n, int lines, int sign, const float* in_dev, float* out_dev,
                            void* stream)
 {

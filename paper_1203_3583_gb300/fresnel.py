@@ -175,3 +175,15 @@ class FresnelFunction(torch.autograd.Function):
         if need_u1 or need_d1:
             plan.adjoint(u1 if need_d1 else None, g2, gu1, gd1)
         return gu1, (gd1.to(ctx.d1_dtype) if need_d1 else None), None
+
+
+def direct_sum(geometry: dict, d1, u1: torch.Tensor, form: int, points, stream=None) -> torch.Tensor:
+    """Direct GPU evaluation of Eq. 2, 5 or 7 (`form`) at destination points
+    (mx, my) (integer arrays or tensors); returns complex64 values.  A reference
+    on sampled points and a measure of the paper's approximations (Eqs. 4, 6)."""
+    mx, my = points
+    dev = u1.device
+    mx_t = torch.as_tensor(mx, dtype=torch.int32, device=dev).contiguous()
+    my_t = torch.as_tensor(my, dtype=torch.int32, device=dev).contiguous()
+    params = capi.make_params(geometry)
+    return capi.asfd_direct_sum(params, _as_cuda_f64(d1), u1, form, mx_t, my_t, stream=stream)
