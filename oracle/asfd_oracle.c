@@ -17,7 +17,9 @@
  * i.e. the discretised Eq. 7 (the Fourier form obtained from Eq. 5 with the
  * destination-chirp approximation of Eq. 6), which is exactly the sum that
  * the NUFT of Eq. 8 evaluates.  u_I = exp(ik d1) is the normally incident
- * plane wave (Sec. 2, after Eq. 3).  The oracle forms u_I and the
+ * plane wave (Sec. 2, after Eq. 3); a plane wave with direction cosines
+ * (sx, sy) gives u_I = exp(ik(sx x + sy y + sz d1)) (geometry fields sx, sy;
+ * the incidence extension of the method).  The oracle forms u_I and the
  * exp(-ik d1) factor of Eq. 5 separately, as written, and accumulates every
  * term in FP64 with no table, no kernel and no FFT.
  *
@@ -56,7 +58,22 @@ typedef struct {
     double p2x, p2y;   /* destination pitch [m]                          */
     double lambda;     /* wavelength [m]                                 */
     double z0;         /* distance between the planes z = 0 and z = z0  */
+    double sx, sy;     /* direction cosines of the incident plane wave   */
 } asfd_oracle_geom;
+
+/* Phase of the incident plane wave u_I = exp(ik(sx x + sy y + sz d1)),
+ * sz = sqrt(1 - sx^2 - sy^2); normal incidence (sx = sy = 0) gives the
+ * exp(ik d1) of Sec. 2. */
+static double incident_phase(const asfd_oracle_geom* g, double k, double x, double y, double h)
+{
+    const double sz = sqrt(1.0 - g->sx * g->sx - g->sy * g->sy);
+    return k * (g->sx * x + g->sy * y + sz * h);
+}
+
+static int bad_geom(const asfd_oracle_geom* g)
+{
+    return !(g->sx * g->sx + g->sy * g->sy < 1.0);
+}
 
 static const double ORACLE_PI = 3.14159265358979323846264338327950288;
 
@@ -99,7 +116,7 @@ static void outer_factor(const asfd_oracle_geom* g, double x2x, double x2y,
 int asfd_oracle_eq7(const asfd_oracle_geom* g, const double* u1, const double* d1,
                     int npts, const int* mx, const int* my, double* out, int nthreads)
 {
-    if (!g || !u1 || !d1 || !mx || !my || !out || npts < 0) return -1;
+    if (!g || !u1 || !d1 || !mx || !my || !out || npts < 0 || bad_geom(g)) return -1;
     const double k = 2.0 * ORACLE_PI / g->lambda;
     const double w = g->p1x * g->p1y;
     set_threads(nthreads);
@@ -116,8 +133,8 @@ int asfd_oracle_eq7(const asfd_oracle_geom* g, const double* u1, const double* d
                 const double x1x = (nx - g->n1x / 2) * g->p1x;
                 const double h = d1[n];
                 const double r0 = g->z0 - h;
-                /* incident plane wave u_I = exp(ik d1) */
-                const double ph_inc = k * h;
+                /* incident plane wave u_I */
+                const double ph_inc = incident_phase(g, k, x1x, x1y, h);
                 /* exp(ik(-d1 + |x1|^2/(2 r0))) */
                 const double ph_src = k * (-h + (x1x * x1x + x1y * x1y) / (2.0 * r0));
                 /* exp(-ik x1.x2 / r0) */
@@ -156,7 +173,7 @@ int asfd_oracle_eq7(const asfd_oracle_geom* g, const double* u1, const double* d
 int asfd_oracle_eq5(const asfd_oracle_geom* g, const double* u1, const double* d1,
                     int npts, const int* mx, const int* my, double* out, int nthreads)
 {
-    if (!g || !u1 || !d1 || !mx || !my || !out || npts < 0) return -1;
+    if (!g || !u1 || !d1 || !mx || !my || !out || npts < 0 || bad_geom(g)) return -1;
     const double k = 2.0 * ORACLE_PI / g->lambda;
     const double w = g->p1x * g->p1y;
     set_threads(nthreads);
@@ -174,7 +191,7 @@ int asfd_oracle_eq5(const asfd_oracle_geom* g, const double* u1, const double* d
                 const double x1x = (nx - g->n1x / 2) * g->p1x;
                 const double h = d1[n];
                 const double r0 = g->z0 - h;
-                const double ph_inc = k * h;  /* u_I = exp(ik d1) */
+                const double ph_inc = incident_phase(g, k, x1x, x1y, h);  /* u_I */
                 const double ph_src = k * (-h + (x1x * x1x + x1y * x1y) / (2.0 * r0));
                 const double ph_x = -k * (x1x * x2x + x1y * x2y) / r0;
                 const double ph_dst = k * x2sq / (2.0 * r0);
@@ -210,7 +227,7 @@ int asfd_oracle_eq5(const asfd_oracle_geom* g, const double* u1, const double* d
 int asfd_oracle_eq2(const asfd_oracle_geom* g, const double* u1, const double* d1,
                     int npts, const int* mx, const int* my, double* out, int nthreads)
 {
-    if (!g || !u1 || !d1 || !mx || !my || !out || npts < 0) return -1;
+    if (!g || !u1 || !d1 || !mx || !my || !out || npts < 0 || bad_geom(g)) return -1;
     const double k = 2.0 * ORACLE_PI / g->lambda;
     const double w = g->p1x * g->p1y;
     set_threads(nthreads);
@@ -229,7 +246,7 @@ int asfd_oracle_eq2(const asfd_oracle_geom* g, const double* u1, const double* d
                 const double dx = x2x - x1x, dy = x2y - x1y, dz = g->z0 - h;
                 const double r2 = dx * dx + dy * dy + dz * dz;
                 const double r = sqrt(r2);
-                const double ph = k * h + k * r;
+                const double ph = incident_phase(g, k, x1x, x1y, h) + k * r;
                 const double c = cos(ph) / r2, s = sin(ph) / r2;
                 const double ur = u1[2 * n], ui = u1[2 * n + 1];
                 row_re += ur * c - ui * s;
@@ -256,14 +273,14 @@ int asfd_oracle_eq2(const asfd_oracle_geom* g, const double* u1, const double* d
  * where K_in is the coefficient of u1[n] in u2 at point i (Eq. 7), so that
  * dL = Re sum_n conj(gu1[n]) du1[n] + sum_n gd1[n] dd1[n].
  * The d1-derivative of the phase of Eq. 7 is written out term by term:
- *   d/dd1 [k d1 + k(-d1 + |x1|^2/(2 r0)) - k x1.x2/r0]
- *     = k - k + k|x1|^2/(2 r0^2) - k x1.x2/r0^2      (dr0/dd1 = -1).
+ *   d/dd1 [k(sx x + sy y + sz d1) + k(-d1 + |x1|^2/(2 r0)) - k x1.x2/r0]
+ *     = k sz - k + k|x1|^2/(2 r0^2) - k x1.x2/r0^2      (dr0/dd1 = -1).
  */
 int asfd_oracle_eq7_grad(const asfd_oracle_geom* g, const double* u1, const double* d1,
                          int npts, const int* mx, const int* my, const double* gu2,
                          double* gu1, double* gd1, int nthreads)
 {
-    if (!g || !u1 || !d1 || !mx || !my || !gu2 || npts < 0) return -1;
+    if (!g || !u1 || !d1 || !mx || !my || !gu2 || npts < 0 || bad_geom(g)) return -1;
     const double k = 2.0 * ORACLE_PI / g->lambda;
     const double w = g->p1x * g->p1y;
     const int nsrc = g->n1x * g->n1y;
@@ -288,9 +305,10 @@ int asfd_oracle_eq7_grad(const asfd_oracle_geom* g, const double* u1, const doub
         const double x1y = (ny - g->n1y / 2) * g->p1y;
         const double h = d1[n];
         const double r0 = g->z0 - h;
-        const double ph_inc = k * h;
+        const double ph_inc = incident_phase(g, k, x1x, x1y, h);
         const double ph_src = k * (-h + (x1x * x1x + x1y * x1y) / (2.0 * r0));
-        const double dph_common = k - k + k * (x1x * x1x + x1y * x1y) / (2.0 * r0 * r0);
+        const double sz = sqrt(1.0 - g->sx * g->sx - g->sy * g->sy);
+        const double dph_common = k * sz - k + k * (x1x * x1x + x1y * x1y) / (2.0 * r0 * r0);
         /* S = sum_i conj(O_i) gu2_i exp(-i ph_i)  and
          * D = sum_i conj(O_i) gu2_i exp(-i ph_i) * dph_i/dd1 */
         double s_re = 0.0, s_im = 0.0, d_re = 0.0, d_im = 0.0;

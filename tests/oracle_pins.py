@@ -107,6 +107,31 @@ def pin_gaussian(eq7, c=0.2e-3, n1=64, p1=10e-6, m2x=40, m2y=36, p2x=11e-6, p2y=
     return rel_l2(eq7(g, u1, np.full((n1, n1), c)), ref)
 
 
+def pin_gaussian_tilted(eq7, c=0.15e-3, sx=0.0021, sy=-0.0013, n1=64, p1=10e-6, m2x=40, m2y=36,
+                        p2x=11e-6, p2y=13e-6, lam=633e-9, z0=0.05):
+    """The Gaussian of pin_gaussian lit by a plane wave with direction cosines
+    (sx, sy): u_I = exp(ik(s.x1 + sz c)) on the plane d1 = c.  The linear phase
+    moves the Gaussian integral to x2 - r0 s and the depth term leaves the
+    constant exp(ik c (sz - 1)) next to the exp(-ik c) of Eq. 5.  The tilt
+    keeps the moved beam inside the destination window (r0 |s| ~ 0.1 mm)."""
+    k = 2 * np.pi / lam
+    w0 = n1 * p1 / 10
+    x = _coords(n1, p1)
+    u1 = np.exp(-(x[None, :] ** 2 + x[:, None] ** 2) / w0 ** 2).astype(np.complex128)
+    r0 = z0 - c
+    sz = np.sqrt(1 - sx ** 2 - sy ** 2)
+    a = 1 / w0 ** 2 - 1j * k / (2 * r0)
+    X = _coords(m2x, p2x)[None, :]
+    Y = _coords(m2y, p2y)[:, None]
+    r2s = (X - r0 * sx) ** 2 + (Y - r0 * sy) ** 2
+    integral = (np.pi / a) * np.exp(-(k / r0) ** 2 * r2s / (4 * a))
+    ref = (np.exp(1j * k * (z0 + (X ** 2 + Y ** 2) / (2 * z0))) / (1j * lam * z0)
+           * np.exp(1j * k * c * (sz - 1)) * integral)
+    g = dict(n1x=n1, n1y=n1, p1x=p1, p1y=p1, m2x=m2x, m2y=m2y, p2x=p2x, p2y=p2y, lam=lam, z0=z0,
+             sx=sx, sy=sy)
+    return rel_l2(eq7(g, u1, np.full((n1, n1), c)), ref)
+
+
 def pin_terraces(eq7, n1x=18, n1y=14, p1x=9e-6, p1y=6e-6, m2x=12, m2y=22, p2x=15e-6, p2y=5e-6,
                  lam=532e-9, z0=0.04, seed=13):
     """d1 takes four constant values on random masks.  For one terrace with
@@ -157,6 +182,7 @@ ALL_PINS = {
     "fft_natural_pitch": (pin_fft_natural_pitch, 1e-9),
     "planar_shift": (pin_planar_shift, 1e-9),
     "gaussian": (pin_gaussian, 1e-9),
+    "gaussian_tilted": (pin_gaussian_tilted, 1e-9),
     "terraces": (pin_terraces, 1e-9),
     "single_sample_modulus": (pin_single_sample_modulus, 1e-12),
 }
@@ -176,33 +202,37 @@ def pin_eq5_equals_eq7_flat(eq5, eq2, eq7, n1x=20, n1y=14, p1x=10e-6, p1y=8e-6, 
 
 
 def pin_eq5_planar_shift(eq5, eq2, eq7, c=0.4e-3, n1x=18, n1y=16, p1x=10e-6, p1y=7e-6,
-                         lam=532e-9, z0=0.04, seed=32):
-    """d1 = c: the exponentials of Eq. 5 combine to exp(ik|x1 - x2|^2/(2 (z0 - c)))
-    (u_I and exp(-ik d1) cancel), i.e. planar Fresnel propagation over z0 - c
-    with the prefactor exp(ik z0)/(i lambda z0) instead of
-    exp(ik(z0 - c))/(i lambda (z0 - c)); planar propagation is Eq. 7 at d1 = 0."""
+                         lam=532e-9, z0=0.04, sx=0.017, sy=0.011, seed=32):
+    """d1 = c under a plane wave with direction cosines (sx, sy): the
+    exponentials of Eq. 5 combine to exp(ik s.x1) exp(ik c (sz - 1))
+    exp(ik|x1 - x2|^2/(2 (z0 - c))), i.e. planar Fresnel propagation of the lit
+    field over z0 - c with the prefactor exp(ik z0)/(i lambda z0) instead of
+    exp(ik(z0 - c))/(i lambda (z0 - c)); that propagation is Eq. 7 at d1 = 0."""
     rng = np.random.default_rng(seed)
     u1 = _rng_field(rng, (n1y, n1x)).astype(np.complex128)
     g = dict(n1x=n1x, n1y=n1y, p1x=p1x, p1y=p1y, m2x=14, m2y=20, p2x=11e-6, p2y=13e-6,
-             lam=lam, z0=z0)
+             lam=lam, z0=z0, sx=sx, sy=sy)
     r0 = z0 - c
     gz = dict(g, z0=r0)
     k = 2 * np.pi / lam
-    ref = eq7(gz, u1, np.zeros((n1y, n1x))) * (r0 / z0) * np.exp(1j * k * c)
+    sz = np.sqrt(1 - sx ** 2 - sy ** 2)
+    ref = eq7(gz, u1, np.zeros((n1y, n1x))) * (r0 / z0) * np.exp(1j * k * c * sz)
     return rel_l2(eq5(g, u1, np.full((n1y, n1x), c)), ref)
 
 
 def pin_eq2_depth_shift(eq5, eq2, eq7, c=0.3e-3, n1x=16, n1y=14, p1x=10e-6, p1y=9e-6,
-                        lam=633e-9, z0=0.05, seed=33):
-    """d1 = c: Eq. 2 depends on the surface only through u_I = exp(ikc) and the
-    distance z0 - c, so it equals z0/(z0 - c) exp(ikc) times Eq. 2 of the flat
-    surface at distance z0 - c."""
+                        lam=633e-9, z0=0.05, sx=-0.012, sy=0.02, seed=33):
+    """d1 = c: Eq. 2 depends on the surface height only through u_I =
+    exp(ik(s.x1 + sz c)) and the distance z0 - c, so it equals
+    z0/(z0 - c) exp(ik sz c) times Eq. 2 of the flat surface at distance z0 - c."""
     rng = np.random.default_rng(seed)
     u1 = _rng_field(rng, (n1y, n1x)).astype(np.complex128)
     g = dict(n1x=n1x, n1y=n1y, p1x=p1x, p1y=p1y, m2x=12, m2y=10, p2x=15e-6, p2y=14e-6,
-             lam=lam, z0=z0)
+             lam=lam, z0=z0, sx=sx, sy=sy)
     k = 2 * np.pi / lam
-    ref = eq2(dict(g, z0=z0 - c), u1, np.zeros((n1y, n1x))) * (z0 / (z0 - c)) * np.exp(1j * k * c)
+    sz = np.sqrt(1 - sx ** 2 - sy ** 2)
+    ref = (eq2(dict(g, z0=z0 - c), u1, np.zeros((n1y, n1x))) * (z0 / (z0 - c))
+           * np.exp(1j * k * c * sz))
     return rel_l2(eq2(g, u1, np.full((n1y, n1x), c)), ref)
 
 

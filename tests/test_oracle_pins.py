@@ -160,6 +160,12 @@ MUTANTS = {
     "drop_weight": ("acc_re *= w;\n        acc_im *= w;", "acc_re *= 1.0;\n        acc_im *= 1.0;"),
     "transpose_index": ("const size_t n = (size_t)ny * g->n1x + nx;",
                         "const size_t n = (size_t)nx * g->n1y + ny;"),
+    "tilt_sign": ("return k * (g->sx * x + g->sy * y + sz * h);",
+                  "return k * (-g->sx * x + g->sy * y + sz * h);"),
+    "tilt_depth_cosine": ("return k * (g->sx * x + g->sy * y + sz * h);",
+                          "return k * (g->sx * x + g->sy * y + h);"),
+    "tilt_swap_axes": ("return k * (g->sx * x + g->sy * y + sz * h);",
+                       "return k * (g->sy * x + g->sx * y + sz * h);"),
 }
 
 
@@ -217,8 +223,10 @@ DIRECT_MUTANTS = {
                           "const double ph = ph_src + ph_x + ph_dst;"),
     "eq2_distance_z0": ("const double dx = x2x - x1x, dy = x2y - x1y, dz = g->z0 - h;",
                         "const double dx = x2x - x1x, dy = x2y - x1y, dz = g->z0;"),
-    "eq2_phase_sign": ("const double ph = k * h + k * r;", "const double ph = k * h - k * r;"),
-    "eq2_drop_incident": ("const double ph = k * h + k * r;", "const double ph = k * r;"),
+    "eq2_phase_sign": ("const double ph = incident_phase(g, k, x1x, x1y, h) + k * r;",
+                       "const double ph = incident_phase(g, k, x1x, x1y, h) - k * r;"),
+    "eq2_drop_incident": ("const double ph = incident_phase(g, k, x1x, x1y, h) + k * r;",
+                          "const double ph = k * r;"),
     "eq2_prefactor_sign": ("out[2 * i] = f * acc_im;\n        out[2 * i + 1] = -f * acc_re;",
                            "out[2 * i] = -f * acc_im;\n        out[2 * i + 1] = f * acc_re;"),
 }
