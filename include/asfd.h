@@ -75,6 +75,10 @@ typedef struct {
                          /*   differ from run to run; 1: conflict-free shared-memory    */
                          /*   tiles without atomics where the map allows them (results */
                          /*   bit-identical run to run), shared-memory atomics else     */
+    double incidence_sx, incidence_sy; /* direction cosines of the incident plane wave */
+                         /*   u_I = exp(ik(sx x1 + sy y1 + sz d1)), sz = sqrt(1 - sx^2  */
+                         /*   - sy^2), sx^2 + sy^2 < 1; 0, 0: normal incidence, the     */
+                         /*   exp(ik d1) of Sec. 2 (incidence is an extension)         */
 } asfd_params;
 
 typedef struct asfd_plan_s* asfd_plan;

@@ -49,6 +49,7 @@ class Params(ctypes.Structure):
         ("es_beta", ctypes.c_double),
         ("kind", ctypes.c_int),
         ("deterministic", ctypes.c_int),
+        ("incidence_sx", ctypes.c_double), ("incidence_sy", ctypes.c_double),
     ]
 
 
@@ -218,11 +219,13 @@ def _dev_ptr(t: torch.Tensor, dtype, shape, name):
 
 def make_params(g: dict, sigma: float = 2.0, kernel_width: int = 7, es_beta: float = 0.0,
                 kind: int = ASFD_KERNEL_ES, deterministic: bool = False) -> Params:
-    """asfd_params from a geometry dict (keys of workloads.geometry)."""
+    """asfd_params from a geometry dict (keys of workloads.geometry; optional
+    sx, sy: direction cosines of the incident plane wave)."""
     return Params(int(g["n1x"]), int(g["n1y"]), float(g["p1x"]), float(g["p1y"]),
                   int(g["m2x"]), int(g["m2y"]), float(g["p2x"]), float(g["p2y"]),
                   float(g["lam"]), float(g["z0"]), float(sigma), int(kernel_width),
-                  float(es_beta), int(kind), int(bool(deterministic)))
+                  float(es_beta), int(kind), int(bool(deterministic)),
+                  float(g.get("sx", 0.0)), float(g.get("sy", 0.0)))
 
 
 def asfd_plan_create(params: Params, d1: torch.Tensor, stream=None) -> ctypes.c_void_p:

@@ -9,9 +9,11 @@
 //   I0 = sum_s psi(s - G) b~_s,  I_a = sum_s psi'(s_a - G_a) psi(s_b - G_b) b~_s
 //   dL/du1_n = conj(E_n) I0
 //   dL/dd1_n = Re[i theta'_n c_n conj(I0)] - sum_a G'_{n,a} Re[c_n conj(I_a)]
-// with theta_n = k|x1|^2/(2 r0) = pi a (1 + q) (the incident wave and the
-// exp(-ik d1) of Eq. 5 cancel, so their derivatives k and -k do too),
-// theta' = pi a (1 + q)^2 / z0 and G'_a = s_a (1 + q)^2 / z0, since
+// with theta_n = k|x1|^2/(2 r0) + k d1 (sz - 1) = pi a (1 + q) + pi inc_d q/(1 + q)
+// (at normal incidence the incident wave and the exp(-ik d1) of Eq. 5
+// cancel; a tilted plane wave leaves its depth term, whose derivative is
+// k (sz - 1) = pi inc_d / z0), theta' = pi a (1 + q)^2 / z0 + pi inc_d / z0 and
+// G'_a = s_a (1 + q)^2 / z0, since
 // dq/dd1 = z0 / (z0 - d1)^2 = (1 + q)^2 / z0.  These are the exact
 // derivatives of the discrete forward computation, so <A x, y> = <x, A^H y>
 // holds to rounding.
@@ -38,6 +40,7 @@ struct InterpArgs {
     int nfx, nfy;
     float half_w, beta_log2e, two_over_w, beta;
     float inv_z0;
+    float inc_d;          // incident depth phase, half-turns per unit d1/z0
 };
 
 template <int W>
@@ -81,13 +84,13 @@ __global__ void __launch_bounds__(256) interp_grad_kernel(InterpArgs a)
     // E = c / u1 (unit modulus prefactor)
     Raw e1 = r;
     e1.u = make_float2(1.f, 0.f);
-    const float2 E = sample_value_fast(e1);
+    const float2 E = sample_value_fast(e1, a.inc_d);
     if (a.gu1) a.gu1[n] = make_float2(E.x * i0.x + E.y * i0.y, E.x * i0.y - E.y * i0.x);
     if (a.gd1) {
         const float2 c = make_float2(r.u.x * E.x - r.u.y * E.y, r.u.x * E.y + r.u.y * E.x);
         const float opq = 1.0f + r.q;
         const float k2 = opq * opq * a.inv_z0;
-        const float dtheta = 3.14159265358979f * (r.ex.a + r.ey.a) * k2;
+        const float dtheta = 3.14159265358979f * ((r.ex.a + r.ey.a) * k2 + a.inc_d * a.inv_z0);
         const float gx = r.ex.s * k2, gy = r.ey.s * k2;
         // Re[i t c conj(I0)] = -t Im[c conj(I0)]
         const float im_c_i0 = c.y * i0.x - c.x * i0.y;
@@ -206,13 +209,13 @@ __global__ void __launch_bounds__(128) interp_window_kernel(InterpArgs a, int ro
             iys = fma2(s0, dwy[b], iys);
         }
         // E = c / u1 (unit modulus prefactor)
-        const float2 E = sample_value_fast(make_float2(1.f, 0.f), ex, ey, q);
+        const float2 E = sample_value_fast(make_float2(1.f, 0.f), ex, ey, q, a.inc_d);
         if (a.gu1) a.gu1[n] = make_float2(E.x * i0.x + E.y * i0.y, E.x * i0.y - E.y * i0.x);
         if (a.gd1) {
             const float2 c = make_float2(u.x * E.x - u.y * E.y, u.x * E.y + u.y * E.x);
             const float opq = 1.0f + q;
             const float k2 = opq * opq * a.inv_z0;
-            const float dtheta = 3.14159265358979f * (ex.a + ey.a) * k2;
+            const float dtheta = 3.14159265358979f * ((ex.a + ey.a) * k2 + a.inc_d * a.inv_z0);
             const float gx = ex.s * k2, gy = ey.s * k2;
             const float im_c_i0 = c.y * i0.x - c.x * i0.y;
             const float re_c_ix = c.x * ixs.x + c.y * ixs.y;
@@ -246,6 +249,7 @@ asfd_status launch_interp_grad(asfd_plan_s* P, const float2* u1, float2* gu1, fl
     a.two_over_w = (float)(2.0 / P->w);
     a.beta = (float)P->beta;
     a.inv_z0 = (float)(1.0 / P->prm.z0);
+    a.inc_d = (float)P->inc_d;
     const size_t n = (size_t)P->prm.n1x * P->prm.n1y;
     const unsigned blocks = (unsigned)((n + 255) / 256);
     cudaError_t e = cudaSuccess;

@@ -79,6 +79,7 @@ struct asfd_plan_s {
     int w = 0;
     double beta = 0.0;
     double alpha_x = 0.0, alpha_y = 0.0;  // fine cells per source sample at d1 = 0
+    double inc_d = 0.0;             // incident depth phase in half-turns per unit d1/z0
     double max_abs_eps = 0.0;
 
     // tables (device)

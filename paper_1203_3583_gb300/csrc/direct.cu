@@ -9,10 +9,11 @@
 // FP64 per (sample, point) pair from FP64 per-sample terms, reduced modulo 2
 // exactly (h - 2 rint(h/2)) and evaluated with sincospif on the reduced
 // fraction; products with u1 are FP32 and the sums are accumulated in FP64.
-//   Eq. 7: h = |x1|^2/(lambda r0) - 2 x1.x2/(lambda r0)
-//          (u_I exp(-ik d1) = 1: the incident wave cancels exp(-ik d1))
+//   Eq. 7: h = |x1|^2/(lambda r0) - 2 x1.x2/(lambda r0) + 2 (s.x1 + (sz - 1) d1)/lambda
+//          (the last term is u_I exp(-ik d1) for a plane wave with direction
+//          cosines (sx, sy, sz); zero at normal incidence)
 //   Eq. 5: h = the Eq. 7 phase + |x2|^2/(lambda r0)
-//   Eq. 2: h = 2 (d1 + r)/lambda, amplitude 1/r^2, r = |(x2 - x1, z0 - d1)|
+//   Eq. 2: h = 2 (s.x1 + sz d1 + r)/lambda, amplitude 1/r^2, r = |(x2 - x1, z0 - d1)|
 // Outer factors: p1x p1y exp(ik(z0 + |x2|^2/(2 z0)))/(i lambda z0) (Eq. 7),
 // p1x p1y exp(ik z0)/(i lambda z0) (Eq. 5), p1x p1y z0/(i lambda) (Eq. 2).
 #include <cmath>
@@ -30,10 +31,13 @@ constexpr int kDirectPoints = 8;  // destination points per block (shares the sa
 struct DirectGeom {
     int n1x, n1y, m2x, m2y;
     double p1x, p1y, p2x, p2y, lambda, z0;
+    double sx, sy, sz;  // incident plane wave direction cosines
 };
 
-// per sample: Eq. 5/7 {|x1|^2/(lambda r0), 2 x1x/(lambda r0), 2 x1y/(lambda r0),
-// 1/(lambda r0)}; Eq. 2 {x1x, x1y, z0 - d1, 2 d1/lambda}
+// per sample: Eq. 5/7 {|x1|^2/(lambda r0) + 2 (s.x1 + (sz - 1) d1)/lambda,
+// 2 x1x/(lambda r0), 2 x1y/(lambda r0), 1/(lambda r0)} (the first term carries
+// u_I exp(-ik d1), 1 at normal incidence); Eq. 2 {x1x, x1y, z0 - d1,
+// 2 (s.x1 + sz d1)/lambda} (the phase of u_I)
 __global__ void direct_prep_kernel(DirectGeom g, const double* __restrict__ d1, int form,
                                    double4* __restrict__ out)
 {
@@ -42,11 +46,13 @@ __global__ void direct_prep_kernel(DirectGeom g, const double* __restrict__ d1, 
     const int nx = (int)(n % g.n1x), ny = (int)(n / g.n1x);
     const double x = (nx - g.n1x / 2) * g.p1x, y = (ny - g.n1y / 2) * g.p1y;
     const double h = d1[n];
+    const double lin = g.sx * x + g.sy * y;
     if (form == 2) {
-        out[n] = make_double4(x, y, g.z0 - h, 2.0 * h / g.lambda);
+        out[n] = make_double4(x, y, g.z0 - h, 2.0 * (lin + g.sz * h) / g.lambda);
     } else {
         const double inv = 1.0 / (g.lambda * (g.z0 - h));
-        out[n] = make_double4((x * x + y * y) * inv, 2.0 * x * inv, 2.0 * y * inv, inv);
+        const double inc = 2.0 * (lin + (g.sz - 1.0) * h) / g.lambda;
+        out[n] = make_double4((x * x + y * y) * inv + inc, 2.0 * x * inv, 2.0 * y * inv, inv);
     }
 }
 
@@ -156,7 +162,13 @@ asfd_status direct_sum(const asfd_params* p, const double* d1, const float2* u1,
         if (!(std::isfinite(x) && x > 0.0))
             return fail(ASFD_ERR_ARG, "pitches, wavelength and z0 must be finite and > 0");
     if (npts == 0) return ASFD_OK;
-    DirectGeom g{p->n1x, p->n1y, p->m2x, p->m2y, p->p1x, p->p1y, p->p2x, p->p2y, p->lambda, p->z0};
+    if (!(std::isfinite(p->incidence_sx) && std::isfinite(p->incidence_sy) &&
+          p->incidence_sx * p->incidence_sx + p->incidence_sy * p->incidence_sy < 1.0))
+        return fail(ASFD_ERR_ARG, "incidence direction cosines need sx^2 + sy^2 < 1");
+    const double sz = std::sqrt(1.0 - p->incidence_sx * p->incidence_sx -
+                                p->incidence_sy * p->incidence_sy);
+    DirectGeom g{p->n1x, p->n1y, p->m2x, p->m2y, p->p1x, p->p1y, p->p2x, p->p2y,
+                 p->lambda, p->z0, p->incidence_sx, p->incidence_sy, sz};
     const size_t n = (size_t)p->n1x * p->n1y;
     double4* s = nullptr;
     cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&s), sizeof(double4) * n, st);

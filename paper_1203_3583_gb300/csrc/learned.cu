@@ -249,6 +249,7 @@ struct TGArgs {
     float* tgrad;
     int n1x, n1y, nstx, nfx, nfy;
     float half_w;
+    float inc_d;
 };
 
 __global__ void __launch_bounds__(256) table_grad_kernel(TGArgs a)
@@ -267,7 +268,7 @@ __global__ void __launch_bounds__(256) table_grad_kernel(TGArgs a)
         int l0x, l0y;
         float dx, dy;
         sample_pos(r.ex, r.ey, r.px, r.py, r.q, a.half_w, l0x, l0y, dx, dy);
-        const float2 c = sample_value_fast(r);
+        const float2 c = sample_value_fast(r, a.inc_d);
         float wx[W], wy[W];
         table_weights<W>(a.tab + (size_t)t * kLearnTableSize, dx, dy, wx, wy);
         const float tx = fmaf(2.f, dx, -1.f), ty = fmaf(2.f, dy, -1.f);
@@ -553,6 +554,7 @@ asfd_status learned_gradient(asfd_plan_s* P, const float2* u1, const float2* ref
     a.nfx = P->nfx;
     a.nfy = P->nfy;
     a.half_w = 0.5f * kLearnW;
+    a.inc_d = (float)P->inc_d;
     table_grad_kernel<<<nst, 256, 0, st>>>(a);
     mlp_backward_kernel<<<nst < 256 ? nst : 256, 256, 0, st>>>(P->lparams, P->lfeat, P->lhid,
                                                                 P->ltgrad, nst, P->lgrad);

@@ -22,8 +22,10 @@ __device__ __forceinline__ double reduce_halfturns(double a) { return a - 2.0 * 
 
 // Per-axis source table: chirp exp(i pi x^2/(lambda z0)), its unreduced value
 // in half-turns, the fine-grid offset alpha x~ and its storage-coordinate split.
+// tilt: 2 s / lambda, the incident plane wave's linear phase in half-turns per
+// metre along this axis (0 at normal incidence); e = exp(i pi (a + tilt x1)).
 __global__ void axis_table_kernel(AxisEntry* ae, AxisPos* ap, double* bu, int n, double p,
-                                  double lam_z0, double alpha, int nf)
+                                  double lam_z0, double alpha, int nf, double tilt)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -31,7 +33,7 @@ __global__ void axis_table_kernel(AxisEntry* ae, AxisPos* ap, double* bu, int n,
     const double x1 = xt * p;
     const double a = x1 * x1 / lam_z0;
     double s, c;
-    sincospi(reduce_halfturns(a), &s, &c);
+    sincospi(reduce_halfturns(a) + reduce_halfturns(tilt * x1), &s, &c);
     const double g = alpha * xt;
     const double B = g + 0.5 * (double)nf;
     const double Br = B - (double)nf * floor(B / (double)nf);
@@ -349,6 +351,9 @@ asfd_status plan_validate(const asfd_params* p, int* nfx, int* nfy, double* beta
                     "sigma*m2x and sigma*m2y must be powers of two in [64, 16384]");
     if (p->kernel_width >= ix / 2 || p->kernel_width >= iy / 2)
         return fail(ASFD_ERR_UNSUPPORTED, "kernel wider than half the fine grid");
+    if (!(std::isfinite(p->incidence_sx) && std::isfinite(p->incidence_sy) &&
+          p->incidence_sx * p->incidence_sx + p->incidence_sy * p->incidence_sy < 1.0))
+        return fail(ASFD_ERR_ARG, "incidence direction cosines need sx^2 + sy^2 < 1");
     if (!(std::isfinite(p->es_beta) && p->es_beta >= 0.0))
         return fail(ASFD_ERR_ARG, "es_beta must be finite and >= 0");
     const double pi = 3.14159265358979323846;
@@ -403,9 +408,18 @@ asfd_status plan_build_tables(asfd_plan_s* P, cudaStream_t st)
     P->alpha_x = p.p1x * p.p2x * P->nfx / lam_z0;
     P->alpha_y = p.p1y * p.p2y * P->nfy / lam_z0;
     axis_table_kernel<<<(p.n1x + 255) / 256, 256, 0, st>>>(P->ax, P->px, P->bux, p.n1x, p.p1x,
-                                                            lam_z0, P->alpha_x, P->nfx);
+                                                            lam_z0, P->alpha_x, P->nfx,
+                                                            2.0 * p.incidence_sx / p.lambda);
     axis_table_kernel<<<(p.n1y + 255) / 256, 256, 0, st>>>(P->ay, P->py, P->buy, p.n1y, p.p1y,
-                                                            lam_z0, P->alpha_y, P->nfy);
+                                                            lam_z0, P->alpha_y, P->nfy,
+                                                            2.0 * p.incidence_sy / p.lambda);
+    // the incident wave's depth phase k d1 (sz - 1) (the rest of u_I exp(-ik d1))
+    // in half-turns is inc_d d1/z0 = inc_d q/(1 + q)
+    {
+        const double sz = std::sqrt(1.0 - p.incidence_sx * p.incidence_sx -
+                                    p.incidence_sy * p.incidence_sy);
+        P->inc_d = 2.0 * p.z0 * (sz - 1.0) / p.lambda;
+    }
     ASFD_CUDA(cudaGetLastError());
 
     // ES kernel values at Gauss-Legendre nodes on [0, w/2]

@@ -32,12 +32,21 @@ __device__ __forceinline__ void sample_pos(const AxisEntry& ex, const AxisEntry&
     dy = cfy - fy;
 }
 
-// c = u1 E_x E_y exp(i pi (a_x + a_y) q)
+// Per-sample correction phase in half-turns: the r0 part of the source chirp,
+// (a_x + a_y) q, plus the incident wave's depth term inc_d q/(1 + q) (zero at
+// normal incidence).
+__device__ __forceinline__ float sample_phase(const AxisEntry& ex, const AxisEntry& ey, float q,
+                                              float inc_d)
+{
+    return fmaf(inc_d, __fdividef(q, 1.0f + q), (ex.a + ey.a) * q);
+}
+
+// c = u1 E_x E_y exp(i pi (a_x + a_y) q + i pi inc_d q/(1 + q))
 __device__ __forceinline__ float2 sample_value(float2 u, const AxisEntry& ex, const AxisEntry& ey,
-                                               float q)
+                                               float q, float inc_d)
 {
     float sn, cs;
-    sincospif((ex.a + ey.a) * q, &sn, &cs);
+    sincospif(sample_phase(ex, ey, q, inc_d), &sn, &cs);
     const float2 exy = make_float2(ex.e.x * ey.e.x - ex.e.y * ey.e.y,
                                    ex.e.x * ey.e.y + ex.e.y * ey.e.x);
     const float2 t1 = make_float2(u.x * exy.x - u.y * exy.y, u.x * exy.y + u.y * exy.x);
@@ -112,13 +121,13 @@ __device__ __forceinline__ float es_weight_fast(float z, float two_over_w, float
     return e;
 }
 
-// c = u1 E_x E_y exp(i pi (a_x + a_y) q); the correction phase is reduced
+// c = u1 E_x E_y exp(i pi sample_phase); the correction phase is reduced
 // modulo 2 half-turns exactly in FP32, then evaluated with the MUFU sine and
 // cosine (absolute error ~4e-7 on [-pi, pi]).
 __device__ __forceinline__ float2 sample_value_fast(float2 u, const AxisEntry& ex,
-                                                    const AxisEntry& ey, float q)
+                                                    const AxisEntry& ey, float q, float inc_d)
 {
-    const float ph = (ex.a + ey.a) * q;
+    const float ph = sample_phase(ex, ey, q, inc_d);
     const float red = ph - 2.0f * rintf(0.5f * ph);
     float sn, cs;
     __sincosf(3.14159265358979f * red, &sn, &cs);
@@ -128,9 +137,9 @@ __device__ __forceinline__ float2 sample_value_fast(float2 u, const AxisEntry& e
     return make_float2(t1.x * cs - t1.y * sn, t1.x * sn + t1.y * cs);
 }
 
-__device__ __forceinline__ float2 sample_value_fast(const Raw& r)
+__device__ __forceinline__ float2 sample_value_fast(const Raw& r, float inc_d)
 {
-    return sample_value_fast(r.u, r.ex, r.ey, r.q);
+    return sample_value_fast(r.u, r.ex, r.ey, r.q, inc_d);
 }
 
 }  // namespace asfd

@@ -128,6 +128,7 @@ SpreadArgs make_spread_args(const asfd_plan_s* P, const float2* u1)
     a.sxw_min = P->sxw_min;
     a.dense_rows = P->dense ? P->dense_rows : 0;
     a.dense_items = P->dense ? P->dense_items : 0;
+    a.inc_d = (float)P->inc_d;
     a.half_w = 0.5f * (float)P->w;
     a.beta_log2e = (float)(P->beta * 1.4426950408889634074);
     a.two_over_w = (float)(2.0 / P->w);

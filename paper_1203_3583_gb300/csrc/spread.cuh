@@ -27,6 +27,7 @@ struct SpreadArgs {
     int sxw_min;       // column stride of the register-window kernel
     int dense_rows;    // rows per run of the dense (global-atomic) window kernel (0: not used)
     int dense_items;   // its warp items (32 columns x dense_rows rows each)
+    float inc_d;       // incident depth phase, half-turns per unit d1/z0
     float half_w;      // w/2
     float beta_log2e;  // beta * log2(e)
     float two_over_w;  // 2/w
@@ -106,7 +107,7 @@ __device__ __forceinline__ void colored_tile(const SpreadArgs& a, int t, float2*
                 sample_pos(cur.ex, cur.ey, cur.px, cur.py, cur.q, a.half_w, l0x, l0y, dx, dy);
                 const int cx = l0x - ox, cy = l0y - oy;
                 if (cx > -W && cx < TX && cy > -W && cy < TY) {
-                    const float2 c = sample_value_fast(cur);
+                    const float2 c = sample_value_fast(cur, a.inc_d);
                     float wx[W], wy[W];
                     tap_weights<W, TAB>(a, nx0 + o, ny0 + j, dx, dy, wx, wy);
                     bool colok[W];
@@ -488,7 +489,7 @@ __device__ __forceinline__ void window_tile(const SpreadArgs& a, int t, float2* 
                     R0 = l0y;
                     live = true;
                 }
-                const float2 c = sample_value_fast(ua, ex, ey, qa);
+                const float2 c = sample_value_fast(ua, ex, ey, qa, a.inc_d);
                 window_add<W, WX>(acc, fresh, l0y - R0, l0x - X0, dx, dy, c, a, neg_c2,
                                   [&](int b) {
                                       window_flush<WX, TX, TY>(tile, R0 + b - oy, X0 - ox, cmask,
@@ -644,7 +645,7 @@ __device__ __forceinline__ void window_atomic_item(const SpreadArgs& a, int it, 
             R0 = l0y;
             live = true;
         }
-        const float2 c = sample_value_fast(u, ex, ey, q);
+        const float2 c = sample_value_fast(u, ex, ey, q, a.inc_d);
         if constexpr (TAB) {
             if (ny / kSrcTile != tab_ty) {  // warp-uniform: every lane is on row ny
                 tab_ty = ny / kSrcTile;
@@ -727,7 +728,7 @@ __device__ __forceinline__ void atomic_tile(const SpreadArgs& a, int tile, float
         const bool hitx = (cx0 < kTileX) || (cx0 + W - 1 > mx);
         const bool hity = (cy0 < kTileY) || (cy0 + W - 1 > my);
         if (!(hitx && hity)) continue;
-        const float2 c = sample_value(__ldg(&a.u1[n]), ex, ey, q);
+        const float2 c = sample_value(__ldg(&a.u1[n]), ex, ey, q, a.inc_d);
 
         float wx[W], wyv[W];
         if constexpr (TAB) {

@@ -51,6 +51,10 @@ CASES = {
     "sinusoid64": lambda: W.make("sinusoid64"),
     "ragged": lambda: (W.geometry(50, 38, 10e-6, 7e-6, 64, 32, 12e-6, 9e-6, 532e-9, 0.04), None,
                        None),
+    # a plane wave incident at direction cosines (0.012, -0.02): its depth
+    # term k d1 (sz - 1) adds to the d1 gradient
+    "ragged_tilted": lambda: (dict(W.geometry(50, 38, 10e-6, 7e-6, 64, 32, 12e-6, 9e-6, 532e-9,
+                                              0.04), sx=0.012, sy=-0.02), None, None),
 }
 
 

@@ -75,3 +75,13 @@ def test_direct_sum_empty_point_list():
     out = direct_sum(g, d1, torch.as_tensor(u1, device="cuda"), 7,
                      (np.zeros(0, np.int32), np.zeros(0, np.int32)))
     assert out.numel() == 0
+
+
+@pytest.mark.parametrize("form", [7, 5, 2])
+def test_direct_sum_tilted_incidence(form):
+    g, u1, d1 = W.make("spherical_cap1024")
+    g = dict(g, sx=-0.008, sy=0.013)
+    pts = W.sample_points(g, 40, seed=320 + form)
+    got = direct_sum(g, d1, torch.as_tensor(u1, device="cuda"), form, pts).cpu().numpy()
+    ref = ORACLE[form](g, u1, d1, points=pts)
+    assert rel_l2(got, ref) < TOL_DIRECT, form
