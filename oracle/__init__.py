@@ -51,8 +51,11 @@ def compile_c(src: str, out: str) -> str:
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle into ``oracle/_build/libasfd_oracle.so``."""
+    """Compile the oracle into ``oracle/_build/libasfd_oracle.so`` (and the 1D
+    oracle of ``oracle/line.py`` beside it)."""
     os.makedirs(_BUILD, exist_ok=True)
+    from . import line
+    line.build(force)
     if (not force and os.path.exists(_LIB_PATH)
             and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
         return _LIB_PATH
