@@ -488,6 +488,31 @@ def extra_measurements(args, g, u1, d1, pts, ref_pts, flush, stream):
                    "eq5_vs_eq2 (Eq. 4, r^2 ~ z0^2)": rl(vals[5], vals[2]),
                    "nufft_vs_eq2": rl(nu, vals[2])}}
 
+    # the paper's 1D experiments (Sec. 3; layout readings in workloads.line_*):
+    # the line NUFFT against the 1D oracle, and the paper's comparison of the
+    # method (Eq. 7) with the Huygens sum (Eq. 2) as the largest difference of
+    # the intensities normalised to the Eq. 2 peak
+    from oracle import line as oline
+    from paper_1203_3583_gb300.fresnel import LinePlan
+    lines = {}
+    for shape, (lx, ld, lw) in (("facets", W.line_facets()), ("quadratic", W.line_quadratic())):
+        lg = W.line_geometry()
+        lu = np.ones(lx.size, np.complex128)
+        with LinePlan(lg, lx, ld, lw) as lp:
+            lu_d = torch.as_tensor(lu.astype(np.complex64), device="cuda")
+            out_l = torch.empty(lg["m2"], dtype=torch.complex64, device="cuda")
+            lms = time_device_ms(lambda: lp.execute(lu_d, out=out_l), steps, 3, flush, stream)
+            got = out_l.cpu().numpy().astype(np.complex128)
+        r7 = oline.line(lg, lx, ld, lw, lu, 7)
+        r2 = oline.line(lg, lx, ld, lw, lu, 2)
+        i2 = np.abs(r2) ** 2
+        lines[shape] = {"samples": int(lx.size), "ms": lms,
+                        "rel_l2_vs_oracle_eq7": float(np.linalg.norm(got - r7) / np.linalg.norm(r7)),
+                        "max_intensity_diff_vs_eq2": float(np.max(np.abs(np.abs(got) ** 2 - i2))
+                                                           / np.max(i2))}
+    res["line"] = {"geometry": "1024 samples at 10 um along the surface, 1024 x 10 um "
+                               "destination, 633 nm, z0 1 m", **lines}
+
     ga, ua, da = W.make("tilt_bump4096")
     with FresnelPlan(ga, da) as p:
         ua_d = torch.as_tensor(ua, device="cuda")

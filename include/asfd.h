@@ -301,6 +301,44 @@ const char* asfd_status_string(asfd_status s);
 const char* asfd_last_error(void);
 
 /*
+ * One-dimensional form with explicit source samples (an extension; the
+ * paper's experiments of Sec. 3 are line sources sampled along their arc
+ * length): sample j at x1[j] (metres, any order and spacing) with height
+ * d1[j] (< z0) and quadrature weight w[j] (its extent along x1); destination
+ * x2 = (m - m2/2) p2.  Computes Eq. 7 in one dimension,
+ *   u2(x2) = exp(ik(z0 + x2^2/(2 z0))) / sqrt(i lambda z0)
+ *            * sum_j w u_I u1 exp(ik(-d1 + x1^2/(2 r0))) exp(-ik x1 x2/r0),
+ * r0 = z0 - d1, u_I = exp(ik(s x1 + sz d1)) (s = incidence_s; s = 0 is the
+ * normal incidence of Sec. 2), by a 1D type-1 NUFFT with the ES kernel:
+ * FP64 per-sample prefactor and position at plan time, FP32 spread (float2
+ * atomic adds), Stockham FFT of sigma*m2 points, deconvolution and chirp.
+ */
+typedef struct {
+    int m2;              /* destination samples; even                            */
+    double p2;           /* destination pitch [m]                                */
+    double lambda;       /* wavelength [m]                                       */
+    double z0;           /* source-axis-to-destination distance [m]              */
+    double sigma;        /* oversampling; sigma*m2 a power of two in [64, 16384] */
+    int kernel_width;    /* 2..16                                                */
+    double es_beta;      /* 0 selects 2.30*w at sigma = 2                        */
+    double incidence_s;  /* direction cosine of the incident plane wave, s^2 < 1 */
+} asfd_line_params;
+
+typedef struct asfd_line_plan_s* asfd_line_plan;
+
+/* x1_dev, d1_dev, w_dev: device FP64 [n], read during the call only.
+ * Synchronises `stream` once (argument check).  Errors: ASFD_ERR_ARG (bad
+ * sizes, non-finite samples, d1 >= z0), ASFD_ERR_UNSUPPORTED, ASFD_ERR_NOMEM. */
+asfd_status asfd_line_plan_create(asfd_line_plan* out, const asfd_line_params* p,
+                                  const double* x1_dev, const double* d1_dev, const double* w_dev,
+                                  int n, void* stream);
+/* u1_dev: device complex[n] (in the plan's sample order); u2_dev: device
+ * complex[m2].  Asynchronous on `stream`; calls on one plan must not overlap. */
+asfd_status asfd_line_execute(asfd_line_plan plan, const float* u1_dev, float* u2_dev,
+                              void* stream);
+asfd_status asfd_line_destroy(asfd_line_plan plan);
+
+/*
  * Direct (O(N^2 M^2)) evaluation of the diffraction sums at npts destination
  * points, on the GPU, for measuring the paper's approximations and as a fast
  * reference on sampled points:

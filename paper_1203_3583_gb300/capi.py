@@ -53,6 +53,16 @@ class Params(ctypes.Structure):
     ]
 
 
+class LineParams(ctypes.Structure):
+    """Mirror of asfd_line_params."""
+
+    _fields_ = [
+        ("m2", ctypes.c_int), ("p2", ctypes.c_double), ("lam", ctypes.c_double),
+        ("z0", ctypes.c_double), ("sigma", ctypes.c_double), ("kernel_width", ctypes.c_int),
+        ("es_beta", ctypes.c_double), ("incidence_s", ctypes.c_double),
+    ]
+
+
 class PlanInfo(ctypes.Structure):
     """Mirror of asfd_plan_info."""
 
@@ -100,6 +110,10 @@ SIGNATURES = {
     "asfd_last_error": (ctypes.c_char_p, []),
     "asfd_fft_lines": (_int, [_int, _int, _int, _vp, _vp, _vp]),
     "asfd_direct_sum": (_int, [ctypes.POINTER(Params), _vp, _vp, _int, _int, _vp, _vp, _vp, _vp]),
+    "asfd_line_plan_create": (_int, [ctypes.POINTER(_vp), ctypes.POINTER(LineParams), _vp, _vp,
+                                     _vp, _int, _vp]),
+    "asfd_line_execute": (_int, [_vp, _vp, _vp, _vp]),
+    "asfd_line_destroy": (_int, [_vp]),
     "asfd_fft_lines_noalloc": (_int, [_int, _int, _int, _vp, _vp, _vp]),
     "asfd_learned_param_count": (ctypes.c_size_t, []),
     "asfd_learned_get_params": (_int, [_vp, _vp, ctypes.c_size_t]),
@@ -304,6 +318,27 @@ def asfd_direct_sum(params: Params, d1: torch.Tensor, u1: torch.Tensor, form: in
         _dev_ptr(mx, torch.int32, (npts,), "mx"), _dev_ptr(my, torch.int32, (npts,), "my"),
         _dev_ptr(out, torch.complex64, (npts,), "out"), _stream(stream)))
     return out
+
+
+def asfd_line_plan_create(params: LineParams, x1: torch.Tensor, d1: torch.Tensor,
+                          w: torch.Tensor, stream=None) -> ctypes.c_void_p:
+    n = int(x1.numel())
+    out = ctypes.c_void_p()
+    _check(load().asfd_line_plan_create(
+        ctypes.byref(out), ctypes.byref(params), _dev_ptr(x1, torch.float64, (n,), "x1"),
+        _dev_ptr(d1, torch.float64, (n,), "d1"), _dev_ptr(w, torch.float64, (n,), "w"), n,
+        _stream(stream)))
+    return out
+
+
+def asfd_line_execute(plan, u1: torch.Tensor, u2: torch.Tensor, n: int, m2: int,
+                      stream=None) -> None:
+    _check(load().asfd_line_execute(plan, _dev_ptr(u1, torch.complex64, (n,), "u1"),
+                                    _dev_ptr(u2, torch.complex64, (m2,), "u2"), _stream(stream)))
+
+
+def asfd_line_destroy(plan) -> None:
+    _check(load().asfd_line_destroy(plan))
 
 
 def asfd_fft_lines(x: torch.Tensor, sign: int = -1, out: torch.Tensor | None = None,

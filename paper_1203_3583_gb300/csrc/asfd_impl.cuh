@@ -175,6 +175,9 @@ asfd_status launch_interp_grad(asfd_plan_s* P, const float2* u1, float2* gu1, fl
 
 // plan helpers
 asfd_status plan_validate(const asfd_params* p, int* nfx, int* nfy, double* beta);
+// Gauss-Legendre nodes z_i on [0, w/2] and weighted ES values w_i psi(z_i) for
+// psi_hat(xi) = 2 sum_i w_i psi(z_i) cos(xi z_i); h = [z..., w psi...]; returns nq.
+int es_quadrature(int w, double beta, std::vector<double>& h);
 asfd_status direct_sum(const asfd_params* p, const double* d1, const float2* u1, int form,
                        int npts, const int* mx, const int* my, float2* out, cudaStream_t st);
 asfd_status plan_alloc(asfd_plan_s* P);

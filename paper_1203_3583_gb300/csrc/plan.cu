@@ -321,6 +321,23 @@ asfd_status plan_build_colored(asfd_plan_s* P, bool wraps, cudaStream_t st);
 
 asfd_status plan_alloc_buffer(asfd_plan_s* P, void** p, size_t bytes) { return alloc(P, p, bytes); }
 
+int es_quadrature(int w, double beta, std::vector<double>& h)
+{
+    const int nq = 160;
+    std::vector<double> x, wt;
+    h.assign(2 * nq, 0.0);
+    gauss_legendre(nq, x, wt);
+    const double half = 0.5 * w;
+    for (int i = 0; i < nq; ++i) {
+        const double z = 0.5 * half * (x[i] + 1.0);
+        const double u = z / half;
+        const double psi = std::exp(beta * (std::sqrt(std::max(0.0, 1.0 - u * u)) - 1.0));
+        h[i] = z;
+        h[nq + i] = 0.5 * half * wt[i] * psi;
+    }
+    return nq;
+}
+
 asfd_status plan_validate(const asfd_params* p, int* nfx, int* nfy, double* beta)
 {
     if (!p) return fail(ASFD_ERR_ARG, "params is NULL");
@@ -423,17 +440,8 @@ asfd_status plan_build_tables(asfd_plan_s* P, cudaStream_t st)
     ASFD_CUDA(cudaGetLastError());
 
     // ES kernel values at Gauss-Legendre nodes on [0, w/2]
-    const int nq = 160;
-    std::vector<double> x, wt, h(2 * nq);
-    gauss_legendre(nq, x, wt);
-    const double half = 0.5 * P->w;
-    for (int i = 0; i < nq; ++i) {
-        const double z = 0.5 * half * (x[i] + 1.0);
-        const double u = z / half;
-        const double psi = std::exp(P->beta * (std::sqrt(std::max(0.0, 1.0 - u * u)) - 1.0));
-        h[i] = z;
-        h[nq + i] = 0.5 * half * wt[i] * psi;
-    }
+    std::vector<double> h;
+    const int nq = es_quadrature(P->w, P->beta, h);
     if (!P->quad) {
         asfd_status s = alloc_n(P, &P->quad, 2 * nq);
         if (s != ASFD_OK) return s;

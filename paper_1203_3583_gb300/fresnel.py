@@ -187,3 +187,46 @@ def direct_sum(geometry: dict, d1, u1: torch.Tensor, form: int, points, stream=N
     my_t = torch.as_tensor(my, dtype=torch.int32, device=dev).contiguous()
     params = capi.make_params(geometry)
     return capi.asfd_direct_sum(params, _as_cuda_f64(d1), u1, form, mx_t, my_t, stream=stream)
+
+
+class LinePlan:
+    """One-dimensional form with explicit source samples (x1, d1, w): Eq. 7 on
+    a line source sampled at arbitrary positions (e.g. along the arc length
+    of tilted facets or a curve), evaluated by a 1D NUFFT on the GPU.
+
+    line: dict with m2, p2, lam, z0 and optional s (incidence direction cosine).
+    """
+
+    def __init__(self, line: dict, x1, d1, w, sigma: float = 2.0, kernel_width: int = 7,
+                 es_beta: float = 0.0, stream=None):
+        self.n = int(np.asarray(x1).size)
+        self.m2 = int(line["m2"])
+        self.params = capi.LineParams(self.m2, float(line["p2"]), float(line["lam"]),
+                                      float(line["z0"]), float(sigma), int(kernel_width),
+                                      float(es_beta), float(line.get("s", 0.0)))
+        t = [_as_cuda_f64(np.ravel(v)) for v in (x1, d1, w)]
+        self._handle = None
+        self._handle = capi.asfd_line_plan_create(self.params, *t, stream=stream)
+
+    def execute(self, u1: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        if out is None:
+            out = torch.empty(self.m2, dtype=torch.complex64, device=u1.device)
+        capi.asfd_line_execute(self._handle, u1, out, self.n, self.m2, stream)
+        return out
+
+    def close(self) -> None:
+        if self._handle is not None:
+            capi.asfd_line_destroy(self._handle)
+            self._handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

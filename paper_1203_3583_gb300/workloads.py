@@ -159,3 +159,63 @@ def sample_points(g, count: int, seed: int):
     total = g["m2x"] * g["m2y"]
     flat = rng.choice(total, size=min(count, total), replace=False)
     return (flat % g["m2x"]).astype(np.int32), (flat // g["m2x"]).astype(np.int32)
+
+
+# --- one-dimensional line sources (explicit samples along the surface) ------------
+
+def line_geometry(m2: int = 1024, p2: float = 10 * UM, lam: float = 633e-9, z0: float = 1.0,
+                  s: float = 0.0) -> dict:
+    """Destination line and light of the paper's 1D experiments (Sec. 3):
+    1024 destination points at 10 um, 633 nm, z0 = 1 m, normal incidence."""
+    return dict(m2=m2, p2=p2, lam=lam, z0=z0, s=s)
+
+
+def line_facets(n_facet: int = 128, p: float = 10 * UM,
+                angles=(-30.0, -50.0, 0.0, 50.0)):
+    """Tilted planar facets sampled every p along the surface (Sec. 3, first
+    experiment).  Reading of the layout, which the paper does not give: four
+    facets of n_facet samples at the given angles to x1, each preceded by a
+    flat segment of n_facet samples (1024 samples in all), heights continuous,
+    the line centred on x1 = 0.  Returns (x1, d1, w) with the projected weight
+    w = p |cos(angle)| of each sample."""
+    steps = []
+    for a in angles:
+        steps += [0.0] * n_facet + [float(a)] * n_facet
+    ang = np.deg2rad(np.array(steps))
+    dx = p * np.cos(ang)
+    dz = p * np.sin(ang)
+    x1 = np.cumsum(dx) - 0.5 * dx
+    d1 = np.cumsum(dz) - 0.5 * dz
+    x1 -= 0.5 * (x1[0] + x1[-1])
+    d1 -= d1.mean()
+    return x1, d1, np.abs(dx)
+
+
+def line_quadratic(n: int = 1024, p: float = 10 * UM, max_slope: float = 1.0):
+    """Quadratic curve d1 = a x1^2 sampled every p along its arc length (Sec. 3,
+    second experiment).  Reading: the paper gives no coefficient; a is chosen so
+    that the slope at the ends of the n samples is max_slope (45 degrees).
+    Returns (x1, d1, w) with w = dx1 of each sample."""
+    half = 0.5 * n * p
+
+    def arclen(x, a):  # closed form of int_0^x sqrt(1 + (2 a t)^2) dt
+        u = 2 * a * x
+        return (u * np.sqrt(1 + u * u) + np.arcsinh(u)) / (4 * a)
+
+    # the end x_e satisfies 2 a x_e = max_slope and arclen(x_e, a) = half
+    m = max_slope
+    a = (m * np.sqrt(1 + m * m) + np.arcsinh(m)) / (4 * half)
+    s_mid = (np.arange(n) - n / 2 + 0.5) * p
+    # invert the (odd, monotone) arc length by bisection on |s|
+    target = np.abs(s_mid)
+    lo, hi = np.zeros(n), np.full(n, 2 * half)
+    for _ in range(80):
+        mid = 0.5 * (lo + hi)
+        big = arclen(mid, a) > target
+        hi = np.where(big, mid, hi)
+        lo = np.where(big, lo, mid)
+    x1 = np.sign(s_mid) * 0.5 * (lo + hi)
+    d1 = a * x1 ** 2
+    d1 -= d1.mean()
+    w = p / np.sqrt(1 + (2 * a * x1) ** 2)
+    return x1, d1, w
