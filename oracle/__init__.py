@@ -37,6 +37,7 @@ class Geom(ctypes.Structure):
         ("p2x", ctypes.c_double), ("p2y", ctypes.c_double),
         ("lam", ctypes.c_double), ("z0", ctypes.c_double),
         ("sx", ctypes.c_double), ("sy", ctypes.c_double),
+        ("ox", ctypes.c_double), ("oy", ctypes.c_double),
     ]
 
 
@@ -101,7 +102,8 @@ def _geom(g: dict) -> Geom:
             raise ValueError(f"{key} must be a positive even integer")
     return Geom(int(g["n1x"]), int(g["n1y"]), float(g["p1x"]), float(g["p1y"]),
                 int(g["m2x"]), int(g["m2y"]), float(g["p2x"]), float(g["p2y"]),
-                float(g["lam"]), float(g["z0"]), float(g.get("sx", 0.0)), float(g.get("sy", 0.0)))
+                float(g["lam"]), float(g["z0"]), float(g.get("sx", 0.0)), float(g.get("sy", 0.0)),
+                float(g.get("ox", 0.0)), float(g.get("oy", 0.0)))
 
 
 def _dptr(a: np.ndarray):

@@ -28,8 +28,10 @@
  *    NUFT definition (Eq. 9) carry a minus sign.  The minus sign is used.
  *  - quadrature weight of the integral over x1: the projected area element
  *    p1x*p1y of the uniform source grid.
- *  - coordinates: x1 = ((nx - N1x/2) p1x, (ny - N1y/2) p1y),
- *                 x2 = ((mx - M2x/2) p2x, (my - M2y/2) p2y).
+ *  - coordinates: x1 = ((nx - N1x/2) p1x, (ny - N1y/2) p1y) + (ox, oy),
+ *                 x2 = ((mx - M2x/2) p2x, (my - M2y/2) p2y); the offset (ox, oy)
+ *                 (zero by default) places a surface off the axis, for sums of
+ *                 several surfaces.
  *  - arrays are row-major [y][x], x fastest; complex values are interleaved
  *    (re, im) FP64 pairs.
  *
@@ -59,6 +61,7 @@ typedef struct {
     double lambda;     /* wavelength [m]                                 */
     double z0;         /* distance between the planes z = 0 and z = z0  */
     double sx, sy;     /* direction cosines of the incident plane wave   */
+    double ox, oy;     /* position of the source grid's centre sample    */
 } asfd_oracle_geom;
 
 /* Phase of the incident plane wave u_I = exp(ik(sx x + sy y + sz d1)),
@@ -126,11 +129,11 @@ int asfd_oracle_eq7(const asfd_oracle_geom* g, const double* u1, const double* d
         const double x2y = (my[i] - g->m2y / 2) * g->p2y;
         double acc_re = 0.0, acc_im = 0.0;
         for (int ny = 0; ny < g->n1y; ++ny) {
-            const double x1y = (ny - g->n1y / 2) * g->p1y;
+            const double x1y = (ny - g->n1y / 2) * g->p1y + g->oy;
             double row_re = 0.0, row_im = 0.0;
             for (int nx = 0; nx < g->n1x; ++nx) {
                 const size_t n = (size_t)ny * g->n1x + nx;
-                const double x1x = (nx - g->n1x / 2) * g->p1x;
+                const double x1x = (nx - g->n1x / 2) * g->p1x + g->ox;
                 const double h = d1[n];
                 const double r0 = g->z0 - h;
                 /* incident plane wave u_I */
@@ -184,11 +187,11 @@ int asfd_oracle_eq5(const asfd_oracle_geom* g, const double* u1, const double* d
         const double x2sq = x2x * x2x + x2y * x2y;
         double acc_re = 0.0, acc_im = 0.0;
         for (int ny = 0; ny < g->n1y; ++ny) {
-            const double x1y = (ny - g->n1y / 2) * g->p1y;
+            const double x1y = (ny - g->n1y / 2) * g->p1y + g->oy;
             double row_re = 0.0, row_im = 0.0;
             for (int nx = 0; nx < g->n1x; ++nx) {
                 const size_t n = (size_t)ny * g->n1x + nx;
-                const double x1x = (nx - g->n1x / 2) * g->p1x;
+                const double x1x = (nx - g->n1x / 2) * g->p1x + g->ox;
                 const double h = d1[n];
                 const double r0 = g->z0 - h;
                 const double ph_inc = incident_phase(g, k, x1x, x1y, h);  /* u_I */
@@ -237,11 +240,11 @@ int asfd_oracle_eq2(const asfd_oracle_geom* g, const double* u1, const double* d
         const double x2y = (my[i] - g->m2y / 2) * g->p2y;
         double acc_re = 0.0, acc_im = 0.0;
         for (int ny = 0; ny < g->n1y; ++ny) {
-            const double x1y = (ny - g->n1y / 2) * g->p1y;
+            const double x1y = (ny - g->n1y / 2) * g->p1y + g->oy;
             double row_re = 0.0, row_im = 0.0;
             for (int nx = 0; nx < g->n1x; ++nx) {
                 const size_t n = (size_t)ny * g->n1x + nx;
-                const double x1x = (nx - g->n1x / 2) * g->p1x;
+                const double x1x = (nx - g->n1x / 2) * g->p1x + g->ox;
                 const double h = d1[n];
                 const double dx = x2x - x1x, dy = x2y - x1y, dz = g->z0 - h;
                 const double r2 = dx * dx + dy * dy + dz * dz;
@@ -301,8 +304,8 @@ int asfd_oracle_eq7_grad(const asfd_oracle_geom* g, const double* u1, const doub
 #pragma omp parallel for schedule(dynamic, 16)
     for (int n = 0; n < nsrc; ++n) {
         const int nx = n % g->n1x, ny = n / g->n1x;
-        const double x1x = (nx - g->n1x / 2) * g->p1x;
-        const double x1y = (ny - g->n1y / 2) * g->p1y;
+        const double x1x = (nx - g->n1x / 2) * g->p1x + g->ox;
+        const double x1y = (ny - g->n1y / 2) * g->p1y + g->oy;
         const double h = d1[n];
         const double r0 = g->z0 - h;
         const double ph_inc = incident_phase(g, k, x1x, x1y, h);

@@ -176,6 +176,27 @@ def pin_single_sample_modulus(eq7, n1=16, p1=10e-6, lam=633e-9, z0=0.05, seed=14
     return float(np.max(np.abs(np.abs(out) - expect)) / expect)
 
 
+def pin_offset_is_padding(eq7, n1x=12, n1y=10, sx_=3, sy_=-2, p1x=10e-6, p1y=8e-6, lam=633e-9,
+                          z0=0.05, seed=15):
+    """A source grid placed off the axis by whole samples, (ox, oy) =
+    (3 p1x, -2 p1y), equals the same samples embedded at shifted indices in a
+    larger zero-padded grid centred on the axis (zero samples add nothing)."""
+    rng = np.random.default_rng(seed)
+    u1 = _rng_field(rng, (n1y, n1x)).astype(np.complex128)
+    d1 = rng.uniform(-40e-6, 40e-6, (n1y, n1x))
+    g = dict(n1x=n1x, n1y=n1y, p1x=p1x, p1y=p1y, m2x=14, m2y=12, p2x=12e-6, p2y=11e-6,
+             lam=lam, z0=z0, ox=sx_ * p1x, oy=sy_ * p1y)
+    big_x, big_y = n1x + 2 * abs(sx_) + 2, n1y + 2 * abs(sy_) + 2
+    ub = np.zeros((big_y, big_x), np.complex128)
+    db = np.zeros((big_y, big_x))
+    x0 = big_x // 2 - n1x // 2 + sx_
+    y0 = big_y // 2 - n1y // 2 + sy_
+    ub[y0:y0 + n1y, x0:x0 + n1x] = u1
+    db[y0:y0 + n1y, x0:x0 + n1x] = d1
+    gb = dict(g, n1x=big_x, n1y=big_y, ox=0.0, oy=0.0)
+    return rel_l2(eq7(g, u1, d1), eq7(gb, ub, db))
+
+
 # Tolerances: the phases k z0 ~ 5e5 rad carry FP64 rounding of ~1e-10 rad, so
 # agreement is bounded near 1e-10; every planted mistake gives O(1) errors.
 ALL_PINS = {
@@ -185,6 +206,7 @@ ALL_PINS = {
     "gaussian_tilted": (pin_gaussian_tilted, 1e-9),
     "terraces": (pin_terraces, 1e-9),
     "single_sample_modulus": (pin_single_sample_modulus, 1e-12),
+    "offset_is_padding": (pin_offset_is_padding, 1e-12),
 }
 
 

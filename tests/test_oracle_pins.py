@@ -151,8 +151,10 @@ MUTANTS = {
                         "const double ph_x = -k * (x1x * x2x + x1y * x2y) / g->z0;\n                const double ph ="),
     "swap_dest_pitch": ("const double x2x = (mx[i] - g->m2x / 2) * g->p2x;\n        const double x2y = (my[i] - g->m2y / 2) * g->p2y;\n        double acc_re",
                         "const double x2x = (mx[i] - g->m2x / 2) * g->p2y;\n        const double x2y = (my[i] - g->m2y / 2) * g->p2x;\n        double acc_re"),
-    "source_origin": ("const double x1x = (nx - g->n1x / 2) * g->p1x;\n                const double h",
-                      "const double x1x = (nx - g->n1x / 2 + 1) * g->p1x;\n                const double h"),
+    "source_origin": ("const double x1x = (nx - g->n1x / 2) * g->p1x + g->ox;\n                const double h",
+                      "const double x1x = (nx - g->n1x / 2 + 1) * g->p1x + g->ox;\n                const double h"),
+    "offset_sign": ("const double x1x = (nx - g->n1x / 2) * g->p1x + g->ox;\n                const double h",
+                    "const double x1x = (nx - g->n1x / 2) * g->p1x - g->ox;\n                const double h"),
     "drop_dest_chirp": ("const double ph = k * (g->z0 + (x2x * x2x + x2y * x2y) / (2.0 * g->z0));",
                         "const double ph = k * (g->z0);"),
     "conj_accumulate": ("row_im += ur * s + ui * c;", "row_im += ur * s - ui * c;"),
