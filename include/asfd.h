@@ -79,6 +79,9 @@ typedef struct {
                          /*   u_I = exp(ik(sx x1 + sy y1 + sz d1)), sz = sqrt(1 - sx^2  */
                          /*   - sy^2), sx^2 + sy^2 < 1; 0, 0: normal incidence, the     */
                          /*   exp(ik d1) of Sec. 2 (incidence is an extension)         */
+    double offset_x, offset_y; /* position [m] of the source grid's centre sample     */
+                         /*   (n1/2): x1 = (n - n1/2) p1 + offset; 0 puts the grid on   */
+                         /*   the axis as in Sec. 2; used to place several surfaces     */
 } asfd_params;
 
 typedef struct asfd_plan_s* asfd_plan;
@@ -299,6 +302,22 @@ const char* asfd_status_string(asfd_status s);
 
 /* Description of the last failure on the calling thread ("" if none). */
 const char* asfd_last_error(void);
+
+/*
+ * Sum of several surfaces' fields at one destination (e.g. the polygons of
+ * a CGH object, each a plan with its own height map, size and position
+ * offset_x/y): u2 = sum_i T_i u1_i.  The surfaces must share m2x, m2y, p2x,
+ * p2y, lambda, z0, sigma, kernel width and beta, and the source sample area
+ * p1x*p1y, and use the default spread (widths up to 7, deterministic = 0,
+ * monotone maps without wrap); they are spread into the first plan's fine
+ * grid and transformed together (one row and one column pass over the union
+ * of their bands).  u1_devs[i]: device complex [n1y_i][n1x_i]; u2_dev:
+ * device complex [m2y][m2x].  Uses the first plan's work buffers: no call on
+ * it may overlap.  Asynchronous on `stream`.  Errors: ASFD_ERR_ARG
+ * (incompatible plans), ASFD_ERR_UNSUPPORTED (not the default spread).
+ */
+asfd_status asfd_multi_execute(const asfd_plan* plans, const float* const* u1_devs, int count,
+                               float* u2_dev, void* stream);
 
 /*
  * One-dimensional form with explicit source samples (an extension; the

@@ -50,6 +50,7 @@ class Params(ctypes.Structure):
         ("kind", ctypes.c_int),
         ("deterministic", ctypes.c_int),
         ("incidence_sx", ctypes.c_double), ("incidence_sy", ctypes.c_double),
+        ("offset_x", ctypes.c_double), ("offset_y", ctypes.c_double),
     ]
 
 
@@ -114,6 +115,7 @@ SIGNATURES = {
                                      _vp, _int, _vp]),
     "asfd_line_execute": (_int, [_vp, _vp, _vp, _vp]),
     "asfd_line_destroy": (_int, [_vp]),
+    "asfd_multi_execute": (_int, [_vp, _vp, _int, _vp, _vp]),
     "asfd_fft_lines_noalloc": (_int, [_int, _int, _int, _vp, _vp, _vp]),
     "asfd_learned_param_count": (ctypes.c_size_t, []),
     "asfd_learned_get_params": (_int, [_vp, _vp, ctypes.c_size_t]),
@@ -234,12 +236,14 @@ def _dev_ptr(t: torch.Tensor, dtype, shape, name):
 def make_params(g: dict, sigma: float = 2.0, kernel_width: int = 7, es_beta: float = 0.0,
                 kind: int = ASFD_KERNEL_ES, deterministic: bool = False) -> Params:
     """asfd_params from a geometry dict (keys of workloads.geometry; optional
-    sx, sy: direction cosines of the incident plane wave)."""
+    sx, sy: direction cosines of the incident plane wave; ox, oy: position of
+    the source grid's centre sample)."""
     return Params(int(g["n1x"]), int(g["n1y"]), float(g["p1x"]), float(g["p1y"]),
                   int(g["m2x"]), int(g["m2y"]), float(g["p2x"]), float(g["p2y"]),
                   float(g["lam"]), float(g["z0"]), float(sigma), int(kernel_width),
                   float(es_beta), int(kind), int(bool(deterministic)),
-                  float(g.get("sx", 0.0)), float(g.get("sy", 0.0)))
+                  float(g.get("sx", 0.0)), float(g.get("sy", 0.0)),
+                  float(g.get("ox", 0.0)), float(g.get("oy", 0.0)))
 
 
 def asfd_plan_create(params: Params, d1: torch.Tensor, stream=None) -> ctypes.c_void_p:
@@ -335,6 +339,18 @@ def asfd_line_execute(plan, u1: torch.Tensor, u2: torch.Tensor, n: int, m2: int,
                       stream=None) -> None:
     _check(load().asfd_line_execute(plan, _dev_ptr(u1, torch.complex64, (n,), "u1"),
                                     _dev_ptr(u2, torch.complex64, (m2,), "u2"), _stream(stream)))
+
+
+def asfd_multi_execute(plans, u1_list, shapes1, u2: torch.Tensor, shape2, stream=None) -> None:
+    n = len(plans)
+    if n < 1 or len(u1_list) != n or len(shapes1) != n:
+        raise ValueError("one u1 per plan")
+    parr = (ctypes.c_void_p * n)(*[ctypes.c_void_p(p.value if hasattr(p, "value") else p)
+                                   for p in plans])
+    uarr = (ctypes.c_void_p * n)(*[_dev_ptr(u, torch.complex64, sh, "u1")
+                                   for u, sh in zip(u1_list, shapes1)])
+    _check(load().asfd_multi_execute(parr, uarr, n, _dev_ptr(u2, torch.complex64, shape2, "u2"),
+                                     _stream(stream)))
 
 
 def asfd_line_destroy(plan) -> None:

@@ -164,6 +164,14 @@ void clear_error();
 
 // stage launchers (each returns ASFD_OK or an error with a message)
 asfd_status launch_spread(asfd_plan_s* P, const float2* u1, cudaStream_t st);
+// dense plans: add the spread of u1 into `grid` (not cleared; another plan's grid)
+asfd_status launch_spread_into(asfd_plan_s* P, const float2* u1, float2* grid, cudaStream_t st);
+// row / column passes over the band rows [ty0, ty1) (and columns [tx0, tx1)) in tiles
+asfd_status launch_fft_rows_band(asfd_plan_s* P, int ty0, int ty1, int tx0, int tx1,
+                                 cudaStream_t st);
+asfd_status launch_fft_cols_band(asfd_plan_s* P, int ty0, int ty1, float2* u2, cudaStream_t st);
+asfd_status multi_execute(asfd_plan_s* const* plans, const float2* const* u1, int count,
+                          float2* u2, cudaStream_t st);
 asfd_status launch_fft_rows(asfd_plan_s* P, cudaStream_t st);
 asfd_status launch_fft_cols(asfd_plan_s* P, float2* u2, cudaStream_t st);
 asfd_status launch_fft_lines(int n, int lines, int sign, const float2* in, float2* out,

@@ -333,6 +333,20 @@ asfd_status asfd_learned_gradient(asfd_plan P, const float* u1_dev, const float*
     });
 }
 
+asfd_status asfd_multi_execute(const asfd_plan* plans, const float* const* u1_devs, int count,
+                               float* u2_dev, void* stream)
+{
+    clear_error();
+    if (!plans || !u1_devs || !u2_dev || count < 1)
+        return fail(ASFD_ERR_ARG, "plans, u1 array and u2 must be non-NULL, count >= 1");
+    for (int i = 0; i < count; ++i)
+        if (!plans[i]) return fail(ASFD_ERR_ARG, "plan is NULL");
+    return on_device(plans[0]->device, [&] {
+        return multi_execute(plans, reinterpret_cast<const float2* const*>(u1_devs), count,
+                             reinterpret_cast<float2*>(u2_dev), static_cast<cudaStream_t>(stream));
+    });
+}
+
 asfd_status asfd_direct_sum(const asfd_params* p, const double* d1_dev, const float* u1_dev,
                             int form, int npts, const int* mx_dev, const int* my_dev,
                             float* out_dev, void* stream)

@@ -32,6 +32,7 @@ struct DirectGeom {
     int n1x, n1y, m2x, m2y;
     double p1x, p1y, p2x, p2y, lambda, z0;
     double sx, sy, sz;  // incident plane wave direction cosines
+    double ox, oy;      // source grid offset
 };
 
 // per sample: Eq. 5/7 {|x1|^2/(lambda r0) + 2 (s.x1 + (sz - 1) d1)/lambda,
@@ -44,7 +45,7 @@ __global__ void direct_prep_kernel(DirectGeom g, const double* __restrict__ d1, 
     const size_t n = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= (size_t)g.n1x * g.n1y) return;
     const int nx = (int)(n % g.n1x), ny = (int)(n / g.n1x);
-    const double x = (nx - g.n1x / 2) * g.p1x, y = (ny - g.n1y / 2) * g.p1y;
+    const double x = (nx - g.n1x / 2) * g.p1x + g.ox, y = (ny - g.n1y / 2) * g.p1y + g.oy;
     const double h = d1[n];
     const double lin = g.sx * x + g.sy * y;
     if (form == 2) {
@@ -168,7 +169,8 @@ asfd_status direct_sum(const asfd_params* p, const double* d1, const float2* u1,
     const double sz = std::sqrt(1.0 - p->incidence_sx * p->incidence_sx -
                                 p->incidence_sy * p->incidence_sy);
     DirectGeom g{p->n1x, p->n1y, p->m2x, p->m2y, p->p1x, p->p1y, p->p2x, p->p2y,
-                 p->lambda, p->z0, p->incidence_sx, p->incidence_sy, sz};
+                 p->lambda, p->z0, p->incidence_sx, p->incidence_sy, sz, p->offset_x,
+                 p->offset_y};
     const size_t n = (size_t)p->n1x * p->n1y;
     double4* s = nullptr;
     cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&s), sizeof(double4) * n, st);

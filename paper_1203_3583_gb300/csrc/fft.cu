@@ -270,6 +270,36 @@ asfd_status launch_fft_cols(asfd_plan_s* P, float2* u2, cudaStream_t st)
     return ASFD_OK;
 }
 
+asfd_status launch_fft_rows_band(asfd_plan_s* P, int ty0, int ty1, int tx0, int tx1,
+                                 cudaStream_t st)
+{
+    RowArgs a = make_row_args(P);
+    a.row0 = ty0 * kTileY;
+    a.nrows = (ty1 - ty0) * kTileY;
+    a.col_lo = tx0 * kTileX;
+    a.col_hi = tx1 * kTileX;
+    if (a.nrows <= 0) return ASFD_OK;
+    cudaError_t e = cudaSuccess;
+#define ASFD_ROWS(L) e = rows_L<L>(a, st)
+    ASFD_FFT_SWITCH(P->nfx, ASFD_ROWS)
+#undef ASFD_ROWS
+    if (e != cudaSuccess) return cuda_fail(e, "fft_rows_kernel launch");
+    return ASFD_OK;
+}
+
+asfd_status launch_fft_cols_band(asfd_plan_s* P, int ty0, int ty1, float2* u2, cudaStream_t st)
+{
+    ColArgs a = make_col_args(P, u2);
+    a.row0 = ty0 * kTileY;
+    a.nrows = (ty1 - ty0) * kTileY;
+    cudaError_t e = cudaSuccess;
+#define ASFD_COLS(L) e = cols_L<L>(a, st)
+    ASFD_FFT_SWITCH(P->nfy, ASFD_COLS)
+#undef ASFD_COLS
+    if (e != cudaSuccess) return cuda_fail(e, "fft_cols_kernel launch");
+    return ASFD_OK;
+}
+
 asfd_status launch_fft_cols_adj(asfd_plan_s* P, const float2* g, cudaStream_t st)
 {
     const int row0 = P->band_ty0 * kTileY;

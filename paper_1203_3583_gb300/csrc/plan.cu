@@ -24,12 +24,13 @@ __device__ __forceinline__ double reduce_halfturns(double a) { return a - 2.0 * 
 // in half-turns, the fine-grid offset alpha x~ and its storage-coordinate split.
 // tilt: 2 s / lambda, the incident plane wave's linear phase in half-turns per
 // metre along this axis (0 at normal incidence); e = exp(i pi (a + tilt x1)).
+// off: position of the centre sample (the grid's offset from the axis, metres).
 __global__ void axis_table_kernel(AxisEntry* ae, AxisPos* ap, double* bu, int n, double p,
-                                  double lam_z0, double alpha, int nf, double tilt)
+                                  double lam_z0, double alpha, int nf, double tilt, double off)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const double xt = (double)(i - n / 2);
+    const double xt = (double)(i - n / 2) + off / p;  // x1 / p
     const double x1 = xt * p;
     const double a = x1 * x1 / lam_z0;
     double s, c;
@@ -373,6 +374,8 @@ asfd_status plan_validate(const asfd_params* p, int* nfx, int* nfy, double* beta
         return fail(ASFD_ERR_ARG, "incidence direction cosines need sx^2 + sy^2 < 1");
     if (!(std::isfinite(p->es_beta) && p->es_beta >= 0.0))
         return fail(ASFD_ERR_ARG, "es_beta must be finite and >= 0");
+    if (!(std::isfinite(p->offset_x) && std::isfinite(p->offset_y)))
+        return fail(ASFD_ERR_ARG, "source offsets must be finite");
     const double pi = 3.14159265358979323846;
     double b = p->es_beta;
     if (b == 0.0)
@@ -426,10 +429,12 @@ asfd_status plan_build_tables(asfd_plan_s* P, cudaStream_t st)
     P->alpha_y = p.p1y * p.p2y * P->nfy / lam_z0;
     axis_table_kernel<<<(p.n1x + 255) / 256, 256, 0, st>>>(P->ax, P->px, P->bux, p.n1x, p.p1x,
                                                             lam_z0, P->alpha_x, P->nfx,
-                                                            2.0 * p.incidence_sx / p.lambda);
+                                                            2.0 * p.incidence_sx / p.lambda,
+                                                            p.offset_x);
     axis_table_kernel<<<(p.n1y + 255) / 256, 256, 0, st>>>(P->ay, P->py, P->buy, p.n1y, p.p1y,
                                                             lam_z0, P->alpha_y, P->nfy,
-                                                            2.0 * p.incidence_sy / p.lambda);
+                                                            2.0 * p.incidence_sy / p.lambda,
+                                                            p.offset_y);
     // the incident wave's depth phase k d1 (sz - 1) (the rest of u_I exp(-ik d1))
     // in half-turns is inc_d d1/z0 = inc_d q/(1 + q)
     {

@@ -136,6 +136,28 @@ SpreadArgs make_spread_args(const asfd_plan_s* P, const float2* u1)
     return a;
 }
 
+asfd_status launch_spread_into(asfd_plan_s* P, const float2* u1, float2* grid, cudaStream_t st)
+{
+    if (!P->dense) return fail(ASFD_ERR_UNSUPPORTED, "accumulating spread needs a dense plan");
+    SpreadArgs a = make_spread_args(P, u1);
+    a.grid = grid;
+    if (a.dense_items <= 0) return ASFD_OK;
+    cudaError_t e = cudaSuccess;
+    if (P->learned) {
+        spread_es_dense_kernel<kLearnW, true><<<(a.dense_items + 3) / 4, 128, 0, st>>>(a, a.dense_items);
+    } else {
+        switch (P->w) {
+#define ASFD_SI(W) case W: spread_es_dense_kernel<W, false><<<(a.dense_items + 3) / 4, 128, 0, st>>>(a, a.dense_items); break;
+            ASFD_SI(2) ASFD_SI(3) ASFD_SI(4) ASFD_SI(5) ASFD_SI(6) ASFD_SI(7)
+#undef ASFD_SI
+            default: return fail(ASFD_ERR_UNSUPPORTED, "dense spread widths are 2..7");
+        }
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "spread kernel launch");
+    return ASFD_OK;
+}
+
 asfd_status launch_spread(asfd_plan_s* P, const float2* u1, cudaStream_t st)
 {
     const SpreadArgs a = make_spread_args(P, u1);

@@ -230,3 +230,15 @@ class LinePlan:
             self.close()
         except Exception:
             pass
+
+
+def multi_execute(plans, u1_list, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Sum of several surfaces' fields at one destination (plans sharing the
+    destination sampling, light, distance, kernel and source sample area; see
+    asfd_multi_execute): one fine grid and one 2D FFT for all of them."""
+    p0 = plans[0]
+    if out is None:
+        out = torch.empty(p0.shape2, dtype=torch.complex64, device=u1_list[0].device)
+    capi.asfd_multi_execute([p.handle for p in plans], u1_list, [p.shape1 for p in plans], out,
+                            p0.shape2, stream)
+    return out

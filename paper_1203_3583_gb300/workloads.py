@@ -219,3 +219,26 @@ def line_quadratic(n: int = 1024, p: float = 10 * UM, max_slope: float = 1.0):
     d1 -= d1.mean()
     w = p / np.sqrt(1 + (2 * a * x1) ** 2)
     return x1, d1, w
+
+
+def make_multi(seed: int = 6):
+    """Several surfaces summed at one destination (a small CGH-like object):
+    three source grids of 384^2, 256^2 and 512^2 samples at 8 um, placed at
+    different positions (offsets), with a spherical cap, a sinusoid and a
+    smooth random surface, random-phase fields; destination 1024^2 at 8 um,
+    532 nm, z0 0.2 m.  Returns a list of (geometry, u1, d1)."""
+    rng = np.random.default_rng(seed)
+    items = []
+    spec = [(384, (-1.2e-3, 0.6e-3), "cap"), (256, (1.0e-3, 1.1e-3), "sin"),
+            (512, (0.2e-3, -0.9e-3), "smooth")]
+    for n, (ox, oy), kind in spec:
+        g = geometry(n, n, 8 * UM, 8 * UM, 1024, 1024, 8 * UM, 8 * UM, 532e-9, 0.2)
+        g = dict(g, ox=ox, oy=oy)
+        if kind == "cap":
+            d1 = surface_spherical_cap(g, 15e-3)
+        elif kind == "sin":
+            d1 = surface_sinusoid(g, 15e-6, 400e-6)
+        else:
+            d1 = surface_smooth_random(g, rng, 30.0, 40e-6)
+        items.append((g, field_random_amp_phase(g, rng), d1))
+    return items
