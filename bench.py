@@ -513,6 +513,28 @@ def extra_measurements(args, g, u1, d1, pts, ref_pts, flush, stream):
     res["line"] = {"geometry": "1024 samples at 10 um along the surface, 1024 x 10 um "
                                "destination, 633 nm, z0 1 m", **lines}
 
+    # several surfaces summed at one destination: one shared grid and FFT
+    # against the surfaces' own transforms one after another
+    from paper_1203_3583_gb300.fresnel import multi_execute
+    mitems = W.make_multi()
+    mplans = [FresnelPlan(gm, dm) for gm, _, dm in mitems]
+    try:
+        mu = [torch.as_tensor(um, device="cuda") for _, um, _ in mitems]
+        mout = torch.empty(mplans[0].shape2, dtype=torch.complex64, device="cuda")
+        souts = [torch.empty(p.shape2, dtype=torch.complex64, device="cuda") for p in mplans]
+        ms_multi = time_device_ms(lambda: multi_execute(mplans, mu, out=mout), steps, 3, flush,
+                                  stream)
+        ms_each = time_device_ms(lambda: [p.execute(u, out=o) for p, u, o in zip(mplans, mu, souts)],
+                                 steps, 3, flush, stream)
+    finally:
+        for p in mplans:
+            p.close()
+    nsm = sum(gm["n1x"] * gm["n1y"] for gm, _, _ in mitems)
+    res["multi"] = {"workload": "3 surfaces (384^2, 256^2, 512^2 at 8 um, offset) -> 1024^2",
+                    "source_samples": nsm, "ms_shared_grid": ms_multi,
+                    "ms_separate_transforms": ms_each,
+                    "samples_per_s": nsm / (ms_multi * 1e-3)}
+
     ga, ua, da = W.make("tilt_bump4096")
     with FresnelPlan(ga, da) as p:
         ua_d = torch.as_tensor(ua, device="cuda")
