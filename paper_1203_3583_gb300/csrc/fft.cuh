@@ -11,7 +11,9 @@
 // last pass writes through a caller storer (crop, deconvolution, scatter), so
 // a line makes exactly one trip through global memory.  Shared memory is
 // padded by one complex per 16 to keep the strided pass writes bank-conflict
-// free.  Twiddles come from a table e^{-2 pi i k/L} built in FP64.
+// free.  Twiddles come from a table e^{-2 pi i k/L} built in FP64 (radix-16
+// passes load four entries per butterfly and form the other eleven by
+// products).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -149,10 +151,31 @@ __device__ __forceinline__ void fft_pass_compute(float2 (&v)[16], int t, const f
         const int j = t + b * TPL;
         if (NS > 1) {
             const int k = j % NS;
+            constexpr int STEP = L / (NS * R);
+            if constexpr (R == 16) {
+                // W^(rk) for r = 1..15 from four table entries (r = 1, 2, 4, 8)
+                // and eleven products: a quarter of the table loads, at most
+                // three roundings more per twiddle
+                float2 w[16];
+                w[1] = __ldg(&tw[k * STEP]);
+                w[2] = __ldg(&tw[2 * k * STEP]);
+                w[4] = __ldg(&tw[4 * k * STEP]);
+                w[8] = __ldg(&tw[8 * k * STEP]);
+                w[3] = cmul(w[1], w[2]);
+                w[5] = cmul(w[4], w[1]);
+                w[6] = cmul(w[4], w[2]);
+                w[7] = cmul(w[4], w[3]);
 #pragma unroll
-            for (int r = 1; r < R; ++r) {
-                const float2 w = __ldg(&tw[r * k * (L / (NS * R))]);
-                v[b * R + r] = S < 0 ? cmul(v[b * R + r], w) : cmulc(v[b * R + r], w);
+                for (int r = 9; r < 16; ++r) w[r] = cmul(w[8], w[r - 8]);
+#pragma unroll
+                for (int r = 1; r < 16; ++r)
+                    v[b * R + r] = S < 0 ? cmul(v[b * R + r], w[r]) : cmulc(v[b * R + r], w[r]);
+            } else {
+#pragma unroll
+                for (int r = 1; r < R; ++r) {
+                    const float2 w = __ldg(&tw[r * k * STEP]);
+                    v[b * R + r] = S < 0 ? cmul(v[b * R + r], w) : cmulc(v[b * R + r], w);
+                }
             }
         }
         dft_reg<R, S>(&v[b * R]);
