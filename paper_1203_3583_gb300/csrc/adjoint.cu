@@ -227,6 +227,23 @@ __global__ void __launch_bounds__(128) interp_window_kernel(InterpArgs a, int ro
 
 }  // namespace
 
+asfd_status interp_window_warp_slots(int w, long long* slots)
+{
+    int dev = 0, sms = 0, per_sm = 0;
+    ASFD_CUDA(cudaGetDevice(&dev));
+    ASFD_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const void* k = nullptr;
+    switch (w) {
+#define ASFD_IWK(W) case W: k = (const void*)interp_window_kernel<W>; break;
+        ASFD_IWK(2) ASFD_IWK(3) ASFD_IWK(4) ASFD_IWK(5) ASFD_IWK(6) ASFD_IWK(7)
+#undef ASFD_IWK
+        default: return fail(ASFD_ERR_UNSUPPORTED, "windowed interpolation widths are 2..7");
+    }
+    ASFD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 128, 0));
+    *slots = (long long)sms * std::max(per_sm, 1) * 4;
+    return ASFD_OK;
+}
+
 asfd_status launch_interp_grad(asfd_plan_s* P, const float2* u1, float2* gu1, float* gd1,
                                cudaStream_t st)
 {
@@ -254,10 +271,12 @@ asfd_status launch_interp_grad(asfd_plan_s* P, const float2* u1, float2* gu1, fl
     const unsigned blocks = (unsigned)((n + 255) / 256);
     cudaError_t e = cudaSuccess;
     if (P->w <= kMaxWindowWidth) {
-        // warp items of 32 columns x `rows` rows, about 2400 of them
+        // warp items of 32 columns x `rows` rows, in whole waves of the resident warps
         const long long ncb = (P->prm.n1x + 31) / 32;
-        const int rows = (int)std::max<long long>(
-            8, std::min<long long>(256, (long long)P->prm.n1y * ncb / 2432));
+        long long slots = 0;
+        const asfd_status s = interp_window_warp_slots(P->w, &slots);
+        if (s != ASFD_OK) return s;
+        const int rows = window_run_rows(P->prm.n1y, ncb, slots);
         const int items = (int)(ncb * ((P->prm.n1y + rows - 1) / rows));
         switch (P->w) {
 #define ASFD_IWW(W) case W: interp_window_kernel<W><<<(items + 3) / 4, 128, 0, st>>>(a, rows, items); break;

@@ -181,6 +181,15 @@ asfd_status launch_fft_rows_adj(asfd_plan_s* P, cudaStream_t st);
 asfd_status launch_interp_grad(asfd_plan_s* P, const float2* u1, float2* gu1, float* gd1,
                                cudaStream_t st);
 
+// Warp-item scheduling of the column-walking window kernels (dense spread,
+// windowed interpolation): warps of the kernel that the current device keeps
+// resident at once (SMs x resident blocks x 4 warps), and the rows per run
+// that make the items of 32 columns x rows fill whole waves of those slots
+// (two waves when the runs stay at least 32 rows long, else one).
+asfd_status dense_spread_warp_slots(int w, bool table, long long* slots);
+asfd_status interp_window_warp_slots(int w, long long* slots);
+int window_run_rows(long long n1y, long long ncb, long long slots);
+
 // plan helpers
 asfd_status plan_validate(const asfd_params* p, int* nfx, int* nfy, double* beta);
 // Gauss-Legendre nodes z_i on [0, w/2] and weighted ES values w_i psi(z_i) for

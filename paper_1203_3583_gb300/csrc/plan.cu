@@ -617,9 +617,12 @@ asfd_status plan_build_colored(asfd_plan_s* P, bool wraps, cudaStream_t st)
     if (monotone && P->w <= kMaxWindowWidth && !p.deterministic) {
         // register windows flushed to the fine grid with float atomics (the
         // fastest path, and the only efficient one for dense maps); runs of
-        // dense_rows rows per lane, enough warp items to fill the GPU
+        // dense_rows rows per lane, in whole waves of the resident warps
         const long long ncb = (p.n1x + 31) / 32;
-        const long long rows = std::max<long long>(8, std::min<long long>(256, p.n1y * ncb / 2432));
+        long long slots = 0;
+        const asfd_status s = dense_spread_warp_slots(P->w, p.kind == ASFD_KERNEL_LEARNED, &slots);
+        if (s != ASFD_OK) return s;
+        const long long rows = window_run_rows(p.n1y, ncb, slots);
         P->dense_rows = (int)rows;
         P->dense_items = (int)(ncb * ((p.n1y + rows - 1) / rows));
         P->dense = true;

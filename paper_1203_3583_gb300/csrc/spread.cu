@@ -102,6 +102,45 @@ cudaError_t launch_table(const SpreadArgs& a, int tiles, bool colored, cudaStrea
 
 }  // namespace
 
+namespace {
+
+asfd_status resident_warps(const void* kernel, long long* slots)
+{
+    int dev = 0, sms = 0, per_sm = 0;
+    ASFD_CUDA(cudaGetDevice(&dev));
+    ASFD_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    ASFD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 128, 0));
+    *slots = (long long)sms * std::max(per_sm, 1) * 4;
+    return ASFD_OK;
+}
+
+}  // namespace
+
+asfd_status dense_spread_warp_slots(int w, bool table, long long* slots)
+{
+    if (table) return resident_warps((const void*)spread_es_dense_kernel<kLearnW, true>, slots);
+    switch (w) {
+#define ASFD_SW(W) case W: return resident_warps((const void*)spread_es_dense_kernel<W, false>, slots);
+        ASFD_SW(2) ASFD_SW(3) ASFD_SW(4) ASFD_SW(5) ASFD_SW(6) ASFD_SW(7)
+#undef ASFD_SW
+        default: return fail(ASFD_ERR_UNSUPPORTED, "dense spread widths are 2..7");
+    }
+}
+
+int window_run_rows(long long n1y, long long ncb, long long slots)
+{
+    // A run's window starts empty and ends with a flush of all its cells, so
+    // runs shorter than about 32 rows pay for that twice as often; uniform
+    // items in whole waves avoid a partly filled last wave.
+    const auto rows_for = [&](long long waves) {
+        const long long runs = std::max<long long>(1, waves * slots / std::max<long long>(ncb, 1));
+        return (n1y + runs - 1) / runs;
+    };
+    long long rows = rows_for(2);
+    if (rows < 32) rows = rows_for(1);
+    return (int)std::max<long long>(8, std::min<long long>(1024, rows));
+}
+
 SpreadArgs make_spread_args(const asfd_plan_s* P, const float2* u1)
 {
     SpreadArgs a;
