@@ -34,6 +34,8 @@ METRIC = "source samples/sec at 2048^2 (forward transform, rel-L2 vs FP64 oracle
 UNIT = "samples/s"
 WORKLOAD = "smooth_random2048"
 FALLBACK_HBM_GBS = 6800.0
+# extra lines after the headline (each on the same single-GPU machine)
+EXTRAS = ("deterministic", "es_widths", "learned", "direct_sum", "line", "multi", "adjoint", "batch")
 
 
 def parse_args():
@@ -49,7 +51,14 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the width sweep, learned kernel, adjoint and batch lines")
-    return ap.parse_args()
+    ap.add_argument("--extras", default="all",
+                    help="comma-separated subset of the extra lines: " + ", ".join(EXTRAS))
+    args = ap.parse_args()
+    args.extras = set(EXTRAS) if args.extras == "all" else set(args.extras.split(","))
+    unknown = args.extras - set(EXTRAS)
+    if unknown:
+        ap.error(f"unknown extras: {sorted(unknown)}")
+    return args
 
 
 def dist_env():
@@ -417,150 +426,160 @@ def extra_measurements(args, g, u1, d1, pts, ref_pts, flush, stream):
         return full, float(np.linalg.norm(got - ref_pts) / np.linalg.norm(ref_pts))
 
     res = {}
-    # the atomic-free (bit-reproducible) spreading path on the same workload
-    with FresnelPlan(g, d1, kernel_width=args.width, deterministic=True) as p:
-        out = torch.empty(p.shape2, dtype=torch.complex64, device="cuda")
-        ms = time_device_ms(lambda: p.execute(u1_d, out=out), steps, 3, flush, stream)
-        sp = time_device_ms(lambda: p.execute_stage(0, u1=u1_d), steps, 3, flush, stream)
-        full, orc = accuracy(out)
-        kind = p.info()["spread_kind"]
-    res["deterministic"] = {"spread_kernel": SPREAD_KERNEL[kind], "samples_per_s": n_src / (ms * 1e-3),
-                            "ms": ms, "spread_ms": sp, "rel_l2_vs_oracle": orc}
     widths = {}
-    for w in (4, 5, 6, 7, 8):
-        with FresnelPlan(g, d1, kernel_width=w) as p:
+    if "deterministic" in args.extras:
+        # the atomic-free (bit-reproducible) spreading path on the same workload
+        with FresnelPlan(g, d1, kernel_width=args.width, deterministic=True) as p:
+            out = torch.empty(p.shape2, dtype=torch.complex64, device="cuda")
+            ms = time_device_ms(lambda: p.execute(u1_d, out=out), steps, 3, flush, stream)
+            sp = time_device_ms(lambda: p.execute_stage(0, u1=u1_d), steps, 3, flush, stream)
+            full, orc = accuracy(out)
+            kind = p.info()["spread_kind"]
+        res["deterministic"] = {"spread_kernel": SPREAD_KERNEL[kind], "samples_per_s": n_src / (ms * 1e-3),
+                                "ms": ms, "spread_ms": sp, "rel_l2_vs_oracle": orc}
+
+    if "es_widths" in args.extras:
+        for w in (4, 5, 6, 7, 8):
+            with FresnelPlan(g, d1, kernel_width=w) as p:
+                out = torch.empty(p.shape2, dtype=torch.complex64, device="cuda")
+                ms = time_device_ms(lambda: p.execute(u1_d, out=out), steps, 3, flush, stream)
+                full, orc = accuracy(out)
+            widths[str(w)] = {"samples_per_s": n_src / (ms * 1e-3), "ms": ms,
+                              "rel_l2_vs_es12": full, "rel_l2_vs_oracle": orc}
+        res["es_widths"] = widths
+
+    if "learned" in args.extras:
+        t0 = time.perf_counter()
+        pairs = L.train_set()
+        model, losses = L.train_model(pairs)
+        torch.cuda.synchronize()
+        train_s = time.perf_counter() - t0
+        with FresnelPlan(g, d1, kind="learned") as p:
+            model.apply_to(p)
             out = torch.empty(p.shape2, dtype=torch.complex64, device="cuda")
             ms = time_device_ms(lambda: p.execute(u1_d, out=out), steps, 3, flush, stream)
             full, orc = accuracy(out)
-        widths[str(w)] = {"samples_per_s": n_src / (ms * 1e-3), "ms": ms,
-                          "rel_l2_vs_es12": full, "rel_l2_vs_oracle": orc}
-    res["es_widths"] = widths
+        match = [w for w in sorted(widths, key=int) if widths[w]["rel_l2_vs_es12"] <= full]
+        res["learned"] = {
+            "kernel_width": 4, "samples_per_s": n_src / (ms * 1e-3), "ms": ms,
+            "rel_l2_vs_es12": full, "rel_l2_vs_oracle": orc,
+            "target_rel_l2": 1e-4, "meets_target": orc <= 1e-4,
+            "gain_vs_es4_error": widths["4"]["rel_l2_vs_es12"] / full if "4" in widths else None,
+            "es_width_at_same_accuracy": int(match[0]) if match else None,
+            "speedup_vs_es_at_same_accuracy": (widths[match[0]]["ms"] / ms) if match else None,
+            "training": {"steps": len(losses), "seconds_incl_references": train_s,
+                         "pairs": len(pairs), "geometry": "smooth_random2048 at 512^2",
+                         "final_train_rel_l2": float(np.sqrt(losses[-1]))}}
 
-    t0 = time.perf_counter()
-    pairs = L.train_set()
-    model, losses = L.train_model(pairs)
-    torch.cuda.synchronize()
-    train_s = time.perf_counter() - t0
-    with FresnelPlan(g, d1, kind="learned") as p:
-        model.apply_to(p)
-        out = torch.empty(p.shape2, dtype=torch.complex64, device="cuda")
-        ms = time_device_ms(lambda: p.execute(u1_d, out=out), steps, 3, flush, stream)
-        full, orc = accuracy(out)
-    match = [w for w in sorted(widths, key=int) if widths[w]["rel_l2_vs_es12"] <= full]
-    res["learned"] = {
-        "kernel_width": 4, "samples_per_s": n_src / (ms * 1e-3), "ms": ms,
-        "rel_l2_vs_es12": full, "rel_l2_vs_oracle": orc,
-        "target_rel_l2": 1e-4, "meets_target": orc <= 1e-4,
-        "gain_vs_es4_error": widths["4"]["rel_l2_vs_es12"] / full,
-        "es_width_at_same_accuracy": int(match[0]) if match else None,
-        "speedup_vs_es_at_same_accuracy": (widths[match[0]]["ms"] / ms) if match else None,
-        "training": {"steps": len(losses), "seconds_incl_references": train_s,
-                     "pairs": len(pairs), "geometry": "smooth_random2048 at 512^2",
-                     "final_train_rel_l2": float(np.sqrt(losses[-1]))}}
+    if "direct_sum" in args.extras:
+        # direct sums of Eq. 7, Eq. 5 and Eq. 2 on sampled points: what the
+        # approximations of Eqs. 4 and 6 cost at this size, and the GPU pair rate
+        from paper_1203_3583_gb300.fresnel import direct_sum
+        pts_d = W.sample_points(g, 512, seed=11)
+        vals, dms = {}, {}
+        for form in (7, 5, 2):
+            direct_sum(g, d1, u1_d, form, pts_d)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            v = direct_sum(g, d1, u1_d, form, pts_d)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            dms[form] = e0.elapsed_time(e1)
+            vals[form] = v.cpu().numpy().astype(np.complex128)
+        with FresnelPlan(g, d1, kernel_width=args.width) as p:
+            nu = p.execute(u1_d).cpu().numpy()[pts_d[1], pts_d[0]].astype(np.complex128)
 
-    # direct sums of Eq. 7, Eq. 5 and Eq. 2 on sampled points: what the
-    # approximations of Eqs. 4 and 6 cost at this size, and the GPU pair rate
-    from paper_1203_3583_gb300.fresnel import direct_sum
-    pts_d = W.sample_points(g, 512, seed=11)
-    vals, dms = {}, {}
-    for form in (7, 5, 2):
-        direct_sum(g, d1, u1_d, form, pts_d)
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        v = direct_sum(g, d1, u1_d, form, pts_d)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        dms[form] = e0.elapsed_time(e1)
-        vals[form] = v.cpu().numpy().astype(np.complex128)
-    with FresnelPlan(g, d1, kernel_width=args.width) as p:
-        nu = p.execute(u1_d).cpu().numpy()[pts_d[1], pts_d[0]].astype(np.complex128)
+        def rl(a, b):
+            return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+        npairs = n_src * len(pts_d[0])
+        res["direct_sum"] = {
+            "points": len(pts_d[0]),
+            "ms": {f"eq{f}": dms[f] for f in dms},
+            "pairs_per_s": {f"eq{f}": npairs / (dms[f] * 1e-3) for f in dms},
+            "rel_l2": {"nufft_vs_eq7": rl(nu, vals[7]), "eq7_vs_eq5 (Eq. 6)": rl(vals[7], vals[5]),
+                       "eq5_vs_eq2 (Eq. 4, r^2 ~ z0^2)": rl(vals[5], vals[2]),
+                       "nufft_vs_eq2": rl(nu, vals[2])}}
 
-    def rl(a, b):
-        return float(np.linalg.norm(a - b) / np.linalg.norm(b))
-    npairs = n_src * len(pts_d[0])
-    res["direct_sum"] = {
-        "points": len(pts_d[0]),
-        "ms": {f"eq{f}": dms[f] for f in dms},
-        "pairs_per_s": {f"eq{f}": npairs / (dms[f] * 1e-3) for f in dms},
-        "rel_l2": {"nufft_vs_eq7": rl(nu, vals[7]), "eq7_vs_eq5 (Eq. 6)": rl(vals[7], vals[5]),
-                   "eq5_vs_eq2 (Eq. 4, r^2 ~ z0^2)": rl(vals[5], vals[2]),
-                   "nufft_vs_eq2": rl(nu, vals[2])}}
+    if "line" in args.extras:
+        # the paper's 1D experiments (Sec. 3; layout readings in workloads.line_*):
+        # the line NUFFT against the 1D oracle, and the paper's comparison of the
+        # method (Eq. 7) with the Huygens sum (Eq. 2) as the largest difference of
+        # the intensities normalised to the Eq. 2 peak
+        from oracle import line as oline
+        from paper_1203_3583_gb300.fresnel import LinePlan
+        lines = {}
+        for shape, (lx, ld, lw) in (("facets", W.line_facets()), ("quadratic", W.line_quadratic())):
+            lg = W.line_geometry()
+            lu = np.ones(lx.size, np.complex128)
+            with LinePlan(lg, lx, ld, lw) as lp:
+                lu_d = torch.as_tensor(lu.astype(np.complex64), device="cuda")
+                out_l = torch.empty(lg["m2"], dtype=torch.complex64, device="cuda")
+                lms = time_device_ms(lambda: lp.execute(lu_d, out=out_l), steps, 3, flush, stream)
+                got = out_l.cpu().numpy().astype(np.complex128)
+            r7 = oline.line(lg, lx, ld, lw, lu, 7)
+            r2 = oline.line(lg, lx, ld, lw, lu, 2)
+            i2 = np.abs(r2) ** 2
+            lines[shape] = {"samples": int(lx.size), "ms": lms,
+                            "rel_l2_vs_oracle_eq7": float(np.linalg.norm(got - r7) / np.linalg.norm(r7)),
+                            "max_intensity_diff_vs_eq2": float(np.max(np.abs(np.abs(got) ** 2 - i2))
+                                                               / np.max(i2))}
+        res["line"] = {"geometry": "1024 samples at 10 um along the surface, 1024 x 10 um "
+                                   "destination, 633 nm, z0 1 m", **lines}
 
-    # the paper's 1D experiments (Sec. 3; layout readings in workloads.line_*):
-    # the line NUFFT against the 1D oracle, and the paper's comparison of the
-    # method (Eq. 7) with the Huygens sum (Eq. 2) as the largest difference of
-    # the intensities normalised to the Eq. 2 peak
-    from oracle import line as oline
-    from paper_1203_3583_gb300.fresnel import LinePlan
-    lines = {}
-    for shape, (lx, ld, lw) in (("facets", W.line_facets()), ("quadratic", W.line_quadratic())):
-        lg = W.line_geometry()
-        lu = np.ones(lx.size, np.complex128)
-        with LinePlan(lg, lx, ld, lw) as lp:
-            lu_d = torch.as_tensor(lu.astype(np.complex64), device="cuda")
-            out_l = torch.empty(lg["m2"], dtype=torch.complex64, device="cuda")
-            lms = time_device_ms(lambda: lp.execute(lu_d, out=out_l), steps, 3, flush, stream)
-            got = out_l.cpu().numpy().astype(np.complex128)
-        r7 = oline.line(lg, lx, ld, lw, lu, 7)
-        r2 = oline.line(lg, lx, ld, lw, lu, 2)
-        i2 = np.abs(r2) ** 2
-        lines[shape] = {"samples": int(lx.size), "ms": lms,
-                        "rel_l2_vs_oracle_eq7": float(np.linalg.norm(got - r7) / np.linalg.norm(r7)),
-                        "max_intensity_diff_vs_eq2": float(np.max(np.abs(np.abs(got) ** 2 - i2))
-                                                           / np.max(i2))}
-    res["line"] = {"geometry": "1024 samples at 10 um along the surface, 1024 x 10 um "
-                               "destination, 633 nm, z0 1 m", **lines}
+    if "multi" in args.extras:
+        # several surfaces summed at one destination: one shared grid and FFT
+        # against the surfaces' own transforms one after another
+        from paper_1203_3583_gb300.fresnel import multi_execute
+        mitems = W.make_multi()
+        mplans = [FresnelPlan(gm, dm) for gm, _, dm in mitems]
+        try:
+            mu = [torch.as_tensor(um, device="cuda") for _, um, _ in mitems]
+            mout = torch.empty(mplans[0].shape2, dtype=torch.complex64, device="cuda")
+            souts = [torch.empty(p.shape2, dtype=torch.complex64, device="cuda") for p in mplans]
+            ms_multi = time_device_ms(lambda: multi_execute(mplans, mu, out=mout), steps, 3, flush,
+                                      stream)
+            ms_each = time_device_ms(lambda: [p.execute(u, out=o) for p, u, o in zip(mplans, mu, souts)],
+                                     steps, 3, flush, stream)
+        finally:
+            for p in mplans:
+                p.close()
+        nsm = sum(gm["n1x"] * gm["n1y"] for gm, _, _ in mitems)
+        res["multi"] = {"workload": "3 surfaces (384^2, 256^2, 512^2 at 8 um, offset) -> 1024^2",
+                        "source_samples": nsm, "ms_shared_grid": ms_multi,
+                        "ms_separate_transforms": ms_each,
+                        "samples_per_s": nsm / (ms_multi * 1e-3)}
 
-    # several surfaces summed at one destination: one shared grid and FFT
-    # against the surfaces' own transforms one after another
-    from paper_1203_3583_gb300.fresnel import multi_execute
-    mitems = W.make_multi()
-    mplans = [FresnelPlan(gm, dm) for gm, _, dm in mitems]
-    try:
-        mu = [torch.as_tensor(um, device="cuda") for _, um, _ in mitems]
-        mout = torch.empty(mplans[0].shape2, dtype=torch.complex64, device="cuda")
-        souts = [torch.empty(p.shape2, dtype=torch.complex64, device="cuda") for p in mplans]
-        ms_multi = time_device_ms(lambda: multi_execute(mplans, mu, out=mout), steps, 3, flush,
-                                  stream)
-        ms_each = time_device_ms(lambda: [p.execute(u, out=o) for p, u, o in zip(mplans, mu, souts)],
-                                 steps, 3, flush, stream)
-    finally:
-        for p in mplans:
-            p.close()
-    nsm = sum(gm["n1x"] * gm["n1y"] for gm, _, _ in mitems)
-    res["multi"] = {"workload": "3 surfaces (384^2, 256^2, 512^2 at 8 um, offset) -> 1024^2",
-                    "source_samples": nsm, "ms_shared_grid": ms_multi,
-                    "ms_separate_transforms": ms_each,
-                    "samples_per_s": nsm / (ms_multi * 1e-3)}
+    if "adjoint" in args.extras:
+        ga, ua, da = W.make("tilt_bump4096")
+        with FresnelPlan(ga, da) as p:
+            ua_d = torch.as_tensor(ua, device="cuda")
+            u2a = p.execute(ua_d)
+            inten = (u2a.abs() ** 2)
+            target = torch.rand(inten.shape, generator=torch.Generator().manual_seed(5)).to("cuda") \
+                * 2 * inten.mean()
+            gu2 = (4 * (inten - target) * u2a).to(torch.complex64)
+            gu1 = torch.empty_like(ua_d)
+            gd1 = torch.empty(p.shape1, dtype=torch.float32, device="cuda")
+            ms = time_device_ms(lambda: p.adjoint(ua_d, gu2, gu1, gd1), steps, 3, flush, stream)
+        res["adjoint"] = {"workload": "tilt_bump4096 (4096^2 at 3.74 um, 532 nm, z0 0.15 m)",
+                          "samples_per_s": ga["n1x"] * ga["n1y"] / (ms * 1e-3), "ms": ms,
+                          "outputs": "dL/du1 (complex) and dL/dd1"}
 
-    ga, ua, da = W.make("tilt_bump4096")
-    with FresnelPlan(ga, da) as p:
-        ua_d = torch.as_tensor(ua, device="cuda")
-        u2a = p.execute(ua_d)
-        inten = (u2a.abs() ** 2)
-        target = torch.rand(inten.shape, generator=torch.Generator().manual_seed(5)).to("cuda") \
-            * 2 * inten.mean()
-        gu2 = (4 * (inten - target) * u2a).to(torch.complex64)
-        gu1 = torch.empty_like(ua_d)
-        gd1 = torch.empty(p.shape1, dtype=torch.float32, device="cuda")
-        ms = time_device_ms(lambda: p.adjoint(ua_d, gu2, gu1, gd1), steps, 3, flush, stream)
-    res["adjoint"] = {"workload": "tilt_bump4096 (4096^2 at 3.74 um, 532 nm, z0 0.15 m)",
-                      "samples_per_s": ga["n1x"] * ga["n1y"] / (ms * 1e-3), "ms": ms,
-                      "outputs": "dL/du1 (complex) and dL/dd1"}
+    if "batch" in args.extras:
+        items = W.make_batch()
+        with FresnelBatch([(gb, db) for gb, _, db in items]) as b:
+            u1s = [torch.as_tensor(ub, device="cuda") for _, ub, _ in items]
+            outs = [torch.empty((gb["m2y"], gb["m2x"]), dtype=torch.complex64, device="cuda")
+                    for gb, _, _ in items]
+            ms = time_device_ms(lambda: b.execute(u1s, out=outs), steps, 3, flush, stream)
+            info = b.info()
+        res["batch"] = {"workload": "rgb_batch24 (24 surfaces, 256^2..2048^2, 450/532/633 nm)",
+                        "samples_per_s": info["source_samples"] / (ms * 1e-3), "ms": ms,
+                        "source_samples": info["source_samples"], "persistent_blocks": info["blocks"],
+                        "cuda_graph": bool(info["graph"])}
 
-    items = W.make_batch()
-    with FresnelBatch([(gb, db) for gb, _, db in items]) as b:
-        u1s = [torch.as_tensor(ub, device="cuda") for _, ub, _ in items]
-        outs = [torch.empty((gb["m2y"], gb["m2x"]), dtype=torch.complex64, device="cuda")
-                for gb, _, _ in items]
-        ms = time_device_ms(lambda: b.execute(u1s, out=outs), steps, 3, flush, stream)
-        info = b.info()
-    res["batch"] = {"workload": "rgb_batch24 (24 surfaces, 256^2..2048^2, 450/532/633 nm)",
-                    "samples_per_s": info["source_samples"] / (ms * 1e-3), "ms": ms,
-                    "source_samples": info["source_samples"], "persistent_blocks": info["blocks"],
-                    "cuda_graph": bool(info["graph"])}
     return res
 
 
