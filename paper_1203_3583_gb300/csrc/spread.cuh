@@ -560,7 +560,7 @@ __device__ __forceinline__ void window_atomic_item(const SpreadArgs& a, int it, 
     // (learned kernel: lanes past the last column follow along without flushing)
     const bool lane_on = !TAB || nx < a.n1x;
     const int nxc = (!TAB || lane_on) ? nx : a.n1x - 1;
-    const int mx = a.nfx - 1, my = a.nfy - 1;
+    const int my = a.nfy - 1;
     const float neg_c2 = -a.two_over_w * a.two_over_w;
     const AxisEntry ex = a.ax[nxc];
     const AxisPos px = a.px[nxc];
@@ -581,10 +581,15 @@ __device__ __forceinline__ void window_atomic_item(const SpreadArgs& a, int it, 
     int R0 = 0;
     bool live = false;
     auto flush_row = [&](int b) {
-        float2* row = a.grid + (size_t)((R0 + b) & my) * a.nfx;
+        // the plan takes this path only when no footprint wraps around the
+        // periodic grid, so the window's columns lie in [0, nfx) and the
+        // addresses are one base plus constant offsets; the clamp keeps every
+        // address inside the row all the same
+        const int xc = min(max(X0, 0), a.nfx - W - maxoff);
+        float2* row = a.grid + (size_t)((R0 + b) & my) * a.nfx + xc;
 #pragma unroll
         for (int i = 0; i < WX; ++i)
-            if (lane_on && i < W + maxoff) atomicAdd(row + ((X0 + i) & mx), acc[b][i]);
+            if (lane_on && i < W + maxoff) atomicAdd(row + i, acc[b][i]);
     };
     // u1 and q of the run's rows are copied asynchronously (cp.async) into a
     // per-lane ring of kDenseRing slots in shared memory, kDenseAhead rows
