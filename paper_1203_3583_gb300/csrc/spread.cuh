@@ -535,10 +535,11 @@ __global__ void __launch_bounds__(32) spread_es_window_kernel(SpreadArgs a)
 // straight to the fine grid with float2 atomic adds (which only need the
 // band zeroed beforehand).  Consecutive samples of a column share their
 // first tap row about 1/(alpha (1 + q)) times, so a row is flushed about
-// alpha times per sample.  Lanes need no step synchronisation.
-constexpr int kDenseAhead = 3;  // rows of u1 and q in flight per lane
+// alpha times per sample.  Lanes need no step synchronisation beyond the
+// warp barrier that publishes each row's table entries.
+constexpr int kDenseAhead = 3;  // rows of u1, q and table entries in flight
 constexpr int kDenseRing = 4;   // ring slots (> kDenseAhead, power of two)
-constexpr int kDenseRingBytes = kDenseRing * 32 * (8 + 4);  // per warp
+constexpr int kDenseRingBytes = kDenseRing * (32 * (8 + 4) + 32);  // per warp
 
 template <int W, bool TAB = false>
 __device__ __forceinline__ void window_atomic_item(const SpreadArgs& a, int it, int lane,
@@ -549,6 +550,10 @@ __device__ __forceinline__ void window_atomic_item(const SpreadArgs& a, int it, 
     const int nx = (it % ncb) * 32 + lane;
     const int ny0 = (it / ncb) * a.dense_rows;
     const int nyl = min(ny0 + a.dense_rows, a.n1y) - 1;
+    // lanes that stay in the item (without the learned kernel, lanes past
+    // the last column return below)
+    const int ncols = a.n1x - (it % ncb) * 32;
+    const unsigned wmask = (TAB || ncols >= 32) ? 0xffffffffu : ((1u << max(ncols, 0)) - 1u);
     if constexpr (TAB) {
         // learned kernel: the warp's lanes span two source-tile columns and
         // step through the same rows, so the two tiles' polynomial tables
@@ -593,9 +598,12 @@ __device__ __forceinline__ void window_atomic_item(const SpreadArgs& a, int it, 
     };
     // u1 and q of the run's rows are copied asynchronously (cp.async) into a
     // per-lane ring of kDenseRing slots in shared memory, kDenseAhead rows
-    // ahead of use
+    // ahead of use, and with them (by lane 0) the row's y table entries,
+    // which every lane of the warp reads
     float2* ring_u = reinterpret_cast<float2*>(ring);
     float* ring_q = reinterpret_cast<float*>(ring_u + kDenseRing * 32);
+    // the row's y table entries (AxisEntry, AxisPos: 24 of 32 bytes per slot), copied by lane 0
+    char* ring_t = reinterpret_cast<char*>(ring_q + kDenseRing * 32);
     auto issue_row = [&](int r) {  // always commits one group (empty past the run)
         if (r <= nyl) {
             const size_t n = (size_t)r * a.n1x + nxc;
@@ -604,6 +612,11 @@ __device__ __forceinline__ void window_atomic_item(const SpreadArgs& a, int it, 
             const unsigned dq = (unsigned)__cvta_generic_to_shared(ring_q + slot * 32 + lane);
             asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(du), "l"(a.u1 + n));
             asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dq), "l"(a.q + n));
+            if (lane == 0) {
+                const unsigned dt = (unsigned)__cvta_generic_to_shared(ring_t + slot * 32);
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(dt), "l"(a.ay + r));
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dt + 16), "l"(a.py + r));
+            }
         }
         asm volatile("cp.async.commit_group;");
     };
@@ -623,12 +636,14 @@ __device__ __forceinline__ void window_atomic_item(const SpreadArgs& a, int it, 
     };
     float4 tnext = load_tab(ny0 / kSrcTile);
     for (int ny = ny0; ny <= nyl; ++ny) {
-        const AxisEntry ey = a.ay[ny];  // the same entry for every lane of the warp
-        const AxisPos py = a.py[ny];
         // this lane's copy of row ny has landed once at most kDenseAhead - 1
-        // younger groups are pending; then queue row ny + kDenseAhead
+        // younger groups are pending (lane 0's table copy is visible to the
+        // warp after the barrier); then queue row ny + kDenseAhead
         asm volatile("cp.async.wait_group %0;" ::"n"(kDenseAhead - 1));
+        __syncwarp(wmask);
         const int slot = (ny - ny0) & (kDenseRing - 1);
+        const AxisEntry ey = *reinterpret_cast<const AxisEntry*>(ring_t + slot * 32);
+        const AxisPos py = *reinterpret_cast<const AxisPos*>(ring_t + slot * 32 + 16);
         const float q = ring_q[slot * 32 + lane];
         const float2 u = ring_u[slot * 32 + lane];
         issue_row(ny + kDenseAhead);
