@@ -185,7 +185,7 @@ STEP_BYTES_PER_SAMPLE = 116
 # DRAM bytes (read + write) per launch of the dominant kernel from one ncu capture
 # of the current kernel (profiles/spread_es_dense_w7_smooth_random2048.md); a
 # kernel or workload without a capture of its current code reports null
-NCU_TRAFFIC = {("spread_es_dense_kernel<7>", "smooth_random2048"): 86.786816e6 + 1.843712e6}
+NCU_TRAFFIC = {("spread_es_dense_kernel<7>", "smooth_random2048"): 86.788864e6 + 1.597696e6}
 
 
 def oracle_sample(g, u1, d1, seconds, seed=7):
