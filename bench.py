@@ -35,7 +35,8 @@ UNIT = "samples/s"
 WORKLOAD = "smooth_random2048"
 FALLBACK_HBM_GBS = 6800.0
 # extra lines after the headline (each on the same single-GPU machine)
-EXTRAS = ("deterministic", "es_widths", "learned", "direct_sum", "line", "multi", "adjoint", "batch")
+EXTRAS = ("deterministic", "es_widths", "learned", "direct_sum", "line", "multi", "adjoint", "batch",
+          "fft_reference")
 
 
 def parse_args():
@@ -566,6 +567,39 @@ def extra_measurements(args, g, u1, d1, pts, ref_pts, flush, stream):
         res["adjoint"] = {"workload": "tilt_bump4096 (4096^2 at 3.74 um, 532 nm, z0 0.15 m)",
                           "samples_per_s": ga["n1x"] * ga["n1y"] / (ms * 1e-3), "ms": ms,
                           "outputs": "dL/du1 (complex) and dL/dd1"}
+
+    if "fft_reference" in args.extras:
+        # cuFFT (through torch.fft) as a timing reference for the two FFT stages:
+        # the full 2D transform of the fine grid, and the same pruning as the
+        # hand-written passes (band rows only, then the kept columns only); the
+        # hand-written column pass also applies the deconvolution, the crop and
+        # the destination chirp, which the cuFFT lines leave out
+        with FresnelPlan(g, d1, kernel_width=args.width) as p:
+            info = p.info()
+            out = torch.empty(p.shape2, dtype=torch.complex64, device="cuda")
+            p.execute_stage(0, u1=u1_d)
+            ours = time_device_ms(lambda: (p.execute_stage(1), p.execute_stage(2, out=out)),
+                                  steps, 3, flush, stream)
+        nfx, nfy, m2x = info["nfx"], info["nfy"], g["m2x"]
+        y0, y1 = info["band_y0"], info["band_y1"]
+        x0, x1 = info["band_x0"], info["band_x1"]
+        gen = torch.Generator(device="cuda").manual_seed(3)
+        grid = torch.zeros((nfy, nfx), dtype=torch.complex64, device="cuda")
+        grid[y0:y1, x0:x1] = torch.randn((y1 - y0, x1 - x0), dtype=torch.complex64, device="cuda",
+                                         generator=gen)
+        full = time_device_ms(lambda: torch.fft.fft2(grid), steps, 3, flush, stream)
+        kept = torch.cat([torch.arange(nfx - m2x // 2, nfx), torch.arange(0, m2x // 2)]).to("cuda")
+        cols = torch.zeros((nfy, m2x), dtype=torch.complex64, device="cuda")
+
+        def pruned():
+            cols[y0:y1] = torch.fft.fft(grid[y0:y1], dim=1).index_select(1, kept)
+            return torch.fft.fft(cols, dim=0)
+        pr = time_device_ms(pruned, steps, 3, flush, stream)
+        res["fft_reference"] = {
+            "library": "cuFFT through torch.fft, timing reference only",
+            "fine_grid": [nfy, nfx], "band_rows": y1 - y0, "kept_columns": m2x,
+            "ms_rows_cols_ours": ours, "ms_cufft_fft2_full_grid": full,
+            "ms_cufft_band_rows_then_kept_columns": pr}
 
     if "batch" in args.extras:
         items = W.make_batch()
