@@ -304,6 +304,22 @@ const char* asfd_status_string(asfd_status s);
 const char* asfd_last_error(void);
 
 /*
+ * Test hooks for the failure paths (no counterpart in the paper; neither
+ * call touches the GPU).
+ *
+ * asfd_debug_fail_allocations(n): the next n device allocations made for 2D
+ * plans (asfd_plan_create, asfd_plan_update_d1, learned tables, batch
+ * surfaces) succeed and every later one fails with ASFD_ERR_NOMEM without
+ * calling the CUDA allocator, until the hook is called again; n < 0 turns it
+ * off (the default).  Process-wide.
+ *
+ * asfd_debug_live_buffers(): the device buffers currently held by all 2D
+ * plans of the process (a failed asfd_plan_create must leave it unchanged).
+ */
+void asfd_debug_fail_allocations(int n);
+long long asfd_debug_live_buffers(void);
+
+/*
  * Sum of several surfaces' fields at one destination (e.g. the polygons of
  * a CGH object, each a plan with its own height map, size and position
  * offset_x/y): u2 = sum_i T_i u1_i.  The surfaces must share m2x, m2y, p2x,

@@ -19,6 +19,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libasfd.so")
 
 ASFD_OK = 0
+ASFD_ERR_ARG = 1
+ASFD_ERR_NOMEM = 3
 ASFD_KERNEL_ES = 0
 ASFD_KERNEL_LEARNED = 1
 
@@ -109,6 +111,8 @@ SIGNATURES = {
     "asfd_destroy": (_int, [_vp]),
     "asfd_status_string": (ctypes.c_char_p, [_int]),
     "asfd_last_error": (ctypes.c_char_p, []),
+    "asfd_debug_fail_allocations": (None, [_int]),
+    "asfd_debug_live_buffers": (ctypes.c_longlong, []),
     "asfd_fft_lines": (_int, [_int, _int, _int, _vp, _vp, _vp]),
     "asfd_direct_sum": (_int, [ctypes.POINTER(Params), _vp, _vp, _int, _int, _vp, _vp, _vp, _vp]),
     "asfd_line_plan_create": (_int, [ctypes.POINTER(_vp), ctypes.POINTER(LineParams), _vp, _vp,

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <cstddef>
+#include <atomic>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -150,6 +151,11 @@ struct asfd_plan_s {
 };
 
 namespace asfd {
+
+// test hooks: allocations of 2D plans still allowed before injected
+// failures (-1: off), and device buffers held by all 2D plans
+extern std::atomic<int> g_alloc_budget;
+extern std::atomic<long long> g_live_buffers;
 
 // error reporting (thread-local message)
 asfd_status fail(asfd_status s, const std::string& msg);

@@ -28,11 +28,15 @@ asfd_status cuda_fail(cudaError_t e, const char* what)
 
 void clear_error() { g_last_error.clear(); }
 
+std::atomic<int> g_alloc_budget{-1};
+std::atomic<long long> g_live_buffers{0};
+
 namespace {
 
 void free_all(asfd_plan_s* P)
 {
     for (auto& b : P->owned) cudaFree(b.p);
+    g_live_buffers -= (long long)P->owned.size();
     P->owned.clear();
     P->device_bytes = 0;
 }
@@ -71,6 +75,10 @@ const char* asfd_status_string(asfd_status s)
 }
 
 const char* asfd_last_error(void) { return g_last_error.c_str(); }
+
+void asfd_debug_fail_allocations(int n) { asfd::g_alloc_budget.store(n < 0 ? -1 : n); }
+
+long long asfd_debug_live_buffers(void) { return asfd::g_live_buffers.load(); }
 
 asfd_status asfd_plan_create(asfd_plan* out, const asfd_params* p, const double* d1_dev,
                              void* stream)

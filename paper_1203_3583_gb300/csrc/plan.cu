@@ -279,8 +279,22 @@ void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& wt)
     }
 }
 
+// true when the allocation-failure hook says this allocation must fail
+bool injected_failure()
+{
+    int b = g_alloc_budget.load();
+    while (b > 0 && !g_alloc_budget.compare_exchange_weak(b, b - 1)) {
+    }
+    return b == 0;
+}
+
 asfd_status alloc(asfd_plan_s* P, void** p, size_t bytes)
 {
+    if (injected_failure()) {
+        *p = nullptr;
+        return fail(ASFD_ERR_NOMEM, "cudaMalloc of " + std::to_string(bytes) +
+                                        " bytes refused by asfd_debug_fail_allocations");
+    }
     cudaError_t e = cudaMalloc(p, bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -290,6 +304,7 @@ asfd_status alloc(asfd_plan_s* P, void** p, size_t bytes)
     }
     P->owned.push_back(DevBuf{*p, bytes});
     P->device_bytes += bytes;
+    ++g_live_buffers;
     return ASFD_OK;
 }
 
@@ -308,6 +323,7 @@ void release(asfd_plan_s* P, void* p)
         if (P->owned[i].p == p) {
             P->device_bytes -= P->owned[i].bytes;
             cudaFree(p);
+            --g_live_buffers;
             P->owned.erase(P->owned.begin() + i);
             return;
         }

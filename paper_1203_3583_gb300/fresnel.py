@@ -117,6 +117,7 @@ class FresnelBatch:
         params = [capi.make_params(g, sigma=sigma, kernel_width=kernel_width,
                                    deterministic=deterministic) for g, _ in items]
         d1s = [_as_cuda_f64(d1) for _, d1 in items]
+        self._handle = None
         self._handle = capi.asfd_batch_create(params, d1s, stream)
 
     def execute(self, u1_list, out=None, stream=None):

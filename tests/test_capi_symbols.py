@@ -88,3 +88,12 @@ def test_invalid_arguments_rejected_on_host(lib_path):
     p = capi.make_params(g)
     assert lib.asfd_plan_create(ctypes.byref(out), ctypes.byref(p), None, None) == 1
     assert b"NULL" in lib.asfd_last_error()
+
+
+def test_debug_hooks_without_gpu(lib_path):
+    """The allocation hook and the live-buffer count touch no device."""
+    from paper_1203_3583_gb300 import capi
+    lib = capi.load(lib_path)
+    assert lib.asfd_debug_live_buffers() >= 0
+    lib.asfd_debug_fail_allocations(2)
+    lib.asfd_debug_fail_allocations(-1)

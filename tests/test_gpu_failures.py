@@ -1,0 +1,82 @@
+"""Failure paths on the GPU without faulting it: the library's allocation
+hook (asfd_debug_fail_allocations) refuses the device allocations of 2D plans
+one after another; every refusal must come back as ASFD_ERR_NOMEM with no
+buffer left behind (asfd_debug_live_buffers), and the plan finally built must
+still match the oracle.  Nothing here makes a kernel fail."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle  # noqa: E402
+from paper_1203_3583_gb300 import capi, workloads as W  # noqa: E402
+from paper_1203_3583_gb300.fresnel import FresnelBatch, FresnelPlan  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1203_3583_gb300 import _build
+    return capi.load(_build.build())
+
+
+def build_with_failures(lib, make, limit=200):
+    """Calls make() with 0, 1, 2, ... allocations allowed; returns the object
+    and the number of allocations it needed."""
+    base = lib.asfd_debug_live_buffers()
+    try:
+        for k in range(limit):
+            lib.asfd_debug_fail_allocations(k)
+            try:
+                obj = make()
+            except capi.AsfdError as e:
+                assert e.status == capi.ASFD_ERR_NOMEM, str(e)
+                assert lib.asfd_debug_live_buffers() == base, f"buffers left after failure {k}"
+                continue
+            return obj, k
+    finally:
+        lib.asfd_debug_fail_allocations(-1)
+    raise AssertionError("still failing after the allocation limit")
+
+
+@pytest.mark.parametrize("deterministic", [False, True])
+def test_plan_allocation_failures_leave_nothing_behind(lib, deterministic):
+    g, u1, d1 = W.make("sinusoid64")
+    base = lib.asfd_debug_live_buffers()
+    plan, needed = build_with_failures(lib, lambda: FresnelPlan(g, d1, deterministic=deterministic))
+    assert needed > 0
+    with plan:
+        assert lib.asfd_debug_live_buffers() > base
+        out = plan.execute(torch.as_tensor(u1, device="cuda")).cpu().numpy()
+    assert lib.asfd_debug_live_buffers() == base
+    ref = oracle.eq7(g, u1, d1)
+    err = float(np.linalg.norm(out - ref) / np.linalg.norm(ref))
+    assert err < 1e-5, err
+
+
+def test_batch_allocation_failures_leave_nothing_behind(lib):
+    g, u1, d1 = W.make("sinusoid64")
+    rng = np.random.default_rng(71)
+    u1b = (rng.standard_normal(u1.shape) + 1j * rng.standard_normal(u1.shape)).astype(np.complex64)
+    items = [(g, u1, d1), (g, u1b, 0.5 * d1)]
+    base = lib.asfd_debug_live_buffers()
+    batch, needed = build_with_failures(lib, lambda: FresnelBatch([(g, d1) for g, _, d1 in items]))
+    assert needed > 0
+    with batch:
+        outs = batch.execute([torch.as_tensor(u, device="cuda") for _, u, _ in items])
+        got = [o.cpu().numpy() for o in outs]
+    assert lib.asfd_debug_live_buffers() == base
+    for (g, u1, d1), out in zip(items, got):
+        ref = oracle.eq7(g, u1, d1)
+        assert float(np.linalg.norm(out - ref) / np.linalg.norm(ref)) < 1e-5
+
+
+def test_hook_off_by_default(lib):
+    g, u1, d1 = W.make("sinusoid64")
+    with FresnelPlan(g, d1):
+        pass
