@@ -245,3 +245,99 @@ def test_planted_mistake_in_direct_sums_fails_a_pin(name, tmp_path):
     failures = [p for p, (fn, tol) in pins.DIRECT_PINS.items()
                 if not fn(*_direct_fns(lib)) < tol]
     assert failures, f"mutant {name} passed every pin"
+
+
+# --- planted mistakes in the gradient routine must fail a gradient pin ----------
+
+def _grad_errors(lib=None):
+    """Worst relative errors of asfd_oracle_eq7_grad (from `lib`) against central
+    differences of the unmodified forward oracle, at normal and tilted incidence,
+    and against the adjoint identity."""
+    errs = {}
+    h = 2e-10
+    for name, seed, tilt in (("d1", 4, (0.0, 0.0)), ("d1_tilted", 7, (0.02, -0.015))):
+        g, u1, d1, target = _grad_case(seed)
+        g = dict(g, sx=tilt[0], sy=tilt[1])
+        u2 = oracle.eq7(g, u1, d1)
+        _, gd1 = oracle.eq7_grad(g, u1, d1, _loss_grad_u2(u2, target), lib=lib)
+        fds, anas = [], []
+        for (iy, ix) in [(0, 0), (3, 7), (7, 9), (5, 2)]:
+            dp = d1.copy()
+            dm = d1.copy()
+            dp[iy, ix] += h
+            dm[iy, ix] -= h
+            fds.append((_loss(g, u1, dp, target) - _loss(g, u1, dm, target)) / (2 * h))
+            anas.append(gd1[iy, ix])
+        fds, anas = np.array(fds), np.array(anas)
+        errs[name] = float(np.max(np.abs(fds - anas)) / np.max(np.abs(fds)))
+    g, u1, d1, target = _grad_case(5)
+    u2 = oracle.eq7(g, u1, d1)
+    gu1, _ = oracle.eq7_grad(g, u1, d1, _loss_grad_u2(u2, target), lib=lib)
+    fds, anas = [], []
+    for (iy, ix) in [(1, 1), (6, 4)]:
+        for unit, part in ((1.0, "re"), (1j, "im")):
+            up = u1.copy()
+            um = u1.copy()
+            up[iy, ix] += 1e-6 * unit
+            um[iy, ix] -= 1e-6 * unit
+            fds.append((_loss(g, up, d1, target) - _loss(g, um, d1, target)) / 2e-6)
+            anas.append(gu1[iy, ix].real if part == "re" else gu1[iy, ix].imag)
+    fds, anas = np.array(fds), np.array(anas)
+    errs["u1"] = float(np.max(np.abs(fds - anas)) / np.max(np.abs(fds)))
+    rng = np.random.default_rng(6)
+    g = dict(n1x=14, n1y=10, p1x=10e-6, p1y=8e-6, m2x=12, m2y=16, p2x=9e-6, p2y=13e-6,
+             lam=532e-9, z0=0.06)
+    x = rng.standard_normal((10, 14)) + 1j * rng.standard_normal((10, 14))
+    y = rng.standard_normal((16, 12)) + 1j * rng.standard_normal((16, 12))
+    d1 = rng.uniform(-2e-4, 4e-4, (10, 14))
+    lhs = np.vdot(y, oracle.eq7(g, x, d1))
+    ahy, _ = oracle.eq7_grad(g, x, d1, y, lib=lib)
+    errs["adjoint"] = float(abs(lhs - np.vdot(ahy, x)) / abs(lhs))
+    return errs
+
+
+GRAD_TOL = {"d1": 1e-4, "d1_tilted": 1e-4, "u1": 1e-5, "adjoint": 1e-12}
+
+
+def test_gradient_pins_hold():
+    errs = _grad_errors()
+    for name, tol in GRAD_TOL.items():
+        assert errs[name] < tol, (name, errs[name])
+
+
+GRAD_MUTANTS = {
+    "grad_source_chirp_sign": (
+        "const double dph_common = k * sz - k + k * (x1x * x1x + x1y * x1y) / (2.0 * r0 * r0);",
+        "const double dph_common = k * sz - k - k * (x1x * x1x + x1y * x1y) / (2.0 * r0 * r0);"),
+    "grad_drop_incident_depth": (
+        "const double dph_common = k * sz - k + k * (x1x * x1x + x1y * x1y) / (2.0 * r0 * r0);",
+        "const double dph_common = k * (x1x * x1x + x1y * x1y) / (2.0 * r0 * r0);"),
+    "grad_cross_sign": (
+        "const double dph = dph_common - k * (x1x * x2x + x1y * x2y) / (r0 * r0);",
+        "const double dph = dph_common + k * (x1x * x2x + x1y * x2y) / (r0 * r0);"),
+    "grad_unconjugated_phase": (
+        "const double t_im = og[2 * i + 1] * c - og[2 * i] * s;",
+        "const double t_im = og[2 * i + 1] * c + og[2 * i] * s;"),
+    "grad_d1_wrong_part": (
+        "gd1[n] = w * (d_re * (-ui) + d_im * ur);",
+        "gd1[n] = w * (d_re * ur + d_im * ui);"),
+    "grad_outer_unconjugated": (
+        "og[2 * i + 1] = o_re * gu2[2 * i + 1] - o_im * gu2[2 * i];",
+        "og[2 * i + 1] = o_re * gu2[2 * i + 1] + o_im * gu2[2 * i];"),
+    "grad_drop_weight": (
+        "gu1[2 * n] = w * s_re;\n            gu1[2 * n + 1] = w * s_im;",
+        "gu1[2 * n] = s_re;\n            gu1[2 * n + 1] = s_im;"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(GRAD_MUTANTS))
+def test_planted_mistake_in_gradient_fails_a_pin(name, tmp_path):
+    src = open(os.path.join(os.path.dirname(oracle.__file__), "asfd_oracle.c")).read()
+    old, new = GRAD_MUTANTS[name]
+    assert src.count(old) == 1, f"mutation anchor for {name} not unique"
+    cpath = tmp_path / "mutant.c"
+    cpath.write_text(src.replace(old, new, 1))
+    lib = oracle.bind(oracle.compile_c(str(cpath), str(tmp_path / "libmutant.so")))
+    errs = _grad_errors(lib)
+    failures = [n for n, tol in GRAD_TOL.items() if not errs[n] < tol]
+    assert failures, f"mutant {name} passed every gradient pin: {errs}"
