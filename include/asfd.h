@@ -14,7 +14,9 @@
  *
  * with x1 = ((nx - N1x/2) p1x, (ny - N1y/2) p1y) and
  *      x2 = ((mx - M2x/2) p2x, (my - M2y/2) p2y).
- * The incident wave exp(ik d1) is the normally incident plane wave of Sec. 2.
+ * The incident wave exp(ik d1) is the normally incident plane wave of Sec. 2;
+ * asfd_params can tilt it (incidence_sx/sy: exp(ik(sx x + sy y + sz d1))) and
+ * move the source grid off the axis (offset_x/y added to x1).
  *
  * Conventions for every entry point:
  *  - Complex arrays are interleaved (re, im) float pairs, row-major [y][x]
