@@ -201,6 +201,7 @@ asfd_status asfd_execute_host(asfd_plan P, const float* u1_host, float* u2_host,
             P->owned.push_back(DevBuf{a, b1});
             P->owned.push_back(DevBuf{b, b2});
             P->device_bytes += b1 + b2;
+            g_live_buffers += 2;
         }
         ASFD_CUDA(cudaMemcpyAsync(P->stage_u1, u1_host, b1, cudaMemcpyHostToDevice, st));
         asfd_status s = launch_spread(P, P->stage_u1, st);
