@@ -85,3 +85,47 @@ def test_sample_points_distinct_and_seeded():
     assert mx.min() >= 0 and mx.max() < 64 and my.min() >= 0 and my.max() < 64
     mx2, my2 = W.sample_points(g, 500, seed=9)
     assert np.array_equal(mx, mx2) and np.array_equal(my, my2)
+
+
+def test_line_facets_layout():
+    x1, d1, w = W.line_facets()
+    p = 10e-6
+    assert x1.size == d1.size == w.size == 1024
+    # samples are the midpoints of 1024 steps of length p along the surface:
+    # p apart within a segment, closer across a change of angle
+    steps = np.hypot(np.diff(x1), np.diff(d1))
+    assert np.all(steps <= p * (1 + 1e-12))
+    # segments: flat, -30, flat, -50, flat, 0, flat, +50 degrees, 128 samples each
+    ang = np.degrees(np.arctan2(np.diff(d1), np.diff(x1)))
+    for k, a in enumerate((0, -30, 0, -50, 0, 0, 0, 50)):
+        inner = slice(k * 128, (k + 1) * 128 - 1)
+        assert np.allclose(steps[inner], p, rtol=1e-9), k
+        assert np.allclose(ang[inner], a, atol=1e-9), (k, a)
+        # projected weight of each sample: p |cos(angle)|
+        assert np.allclose(w[k * 128:(k + 1) * 128], p * abs(math.cos(math.radians(a))), rtol=1e-12)
+    assert abs(0.5 * (x1[0] + x1[-1])) < 1e-15 and abs(d1.mean()) < 1e-15
+
+
+def test_line_quadratic_layout():
+    x1, d1, w = W.line_quadratic()
+    p = 10e-6
+    assert x1.size == 1024 and np.all(np.diff(x1) > 0)
+    # a parabola: constant second difference in x, 45 degree slope at the ends
+    a = np.polyfit(x1, d1, 2)[0]
+    assert np.allclose(d1 - d1.mean(), a * x1 ** 2 - np.mean(a * x1 ** 2), atol=1e-15)
+    end_slope = 2 * a * (x1[-1] + 0.5 * w[-1])
+    assert abs(end_slope - 1.0) < 0.01
+    # samples p apart along the arc
+    steps = np.hypot(np.diff(x1), np.diff(d1))
+    assert np.allclose(steps, p, rtol=1e-3)
+    assert np.allclose(w, p / np.sqrt(1 + (2 * a * x1) ** 2), rtol=1e-9)
+
+
+def test_multi_surfaces():
+    items = W.make_multi()
+    assert [g["n1x"] for g, _, _ in items] == [384, 256, 512]
+    for g, u1, d1 in items:
+        assert (g["m2x"], g["m2y"], g["lam"], g["z0"]) == (1024, 1024, 532e-9, 0.2)
+        assert "ox" in g and "oy" in g and u1.shape == d1.shape == (g["n1y"], g["n1x"])
+    offs = {(g["ox"], g["oy"]) for g, _, _ in items}
+    assert len(offs) == 3
