@@ -34,6 +34,8 @@ METRIC = "source samples/sec at 2048^2 (forward transform, rel-L2 vs FP64 oracle
 UNIT = "samples/s"
 WORKLOAD = "smooth_random2048"
 FALLBACK_HBM_GBS = 6800.0
+# seconds of untimed back-to-back steps under clock sampling before the timed region
+CLOCK_LOAD_S = 0.5
 # extra lines after the headline (each on the same single-GPU machine)
 EXTRAS = ("deterministic", "es_widths", "learned", "direct_sum", "line", "multi", "adjoint", "batch",
           "fft_reference")
@@ -151,7 +153,22 @@ class ClockSampler:
         if not sm:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
-                "samples": len(sm), "window": "warm-up + timed region"}
+                "samples": len(sm),
+                "window": f"warm-up, {CLOCK_LOAD_S} s of the same steps back to back, timed region"}
+
+
+def keep_busy(step, flush, seconds, synchronize, batch=16):
+    """Runs flush.zero_() and step() back to back, untimed, for about `seconds`,
+    synchronising every `batch` steps; returns the number of steps run."""
+    n = 0
+    end = time.perf_counter() + seconds
+    while time.perf_counter() < end:
+        for _ in range(batch):
+            flush.zero_()
+            step()
+            n += 1
+        synchronize()
+    return n
 
 
 def measured_peaks():
@@ -283,7 +300,9 @@ def run_ours(args):
         ev[3].record(stream)
 
     # clocks are sampled from the start of the warm-up to the end of the timed
-    # region (the timed region alone is often shorter than one sample period)
+    # region; the timed region alone is shorter than one sample period, so the
+    # same steps also run back to back (untimed) for about half a second just
+    # before it, and the samples see the GPU under this workload's load
     clocks = ClockSampler(local) if rank == 0 else None
     if clocks:
         clocks.wait_first_sample()
@@ -291,6 +310,9 @@ def run_ours(args):
         flush.zero_()
         step([torch.cuda.Event(enable_timing=True) for _ in range(4)])
     torch.cuda.synchronize()
+    if clocks:
+        load_evs = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        keep_busy(lambda: step(load_evs), flush, CLOCK_LOAD_S, torch.cuda.synchronize)
     plan.check_device_status()
 
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]

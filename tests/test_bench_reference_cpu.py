@@ -30,3 +30,30 @@ def test_reference_arm_prints_contract_line():
     assert line["e2e"] == {"value": line["value"], "unit": line["unit"],
                            "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
     assert line["config"]["workload"] == "sinusoid64"
+
+
+def test_keep_busy_runs_steps_for_the_requested_time():
+    """The untimed load before the timed region (so that the clock samples see
+    the GPU under load) runs whole batches of flush + step and synchronises."""
+    import time
+
+    sys.path.insert(0, ROOT)
+    import bench
+
+    calls = {"flush": 0, "step": 0, "sync": 0}
+
+    class Flush:
+        def zero_(self):
+            calls["flush"] += 1
+
+    def step():
+        calls["step"] += 1
+
+    def sync():
+        calls["sync"] += 1
+
+    t = time.perf_counter()
+    n = bench.keep_busy(step, Flush(), 0.05, sync, batch=4)
+    assert time.perf_counter() - t >= 0.05
+    assert n == calls["step"] == calls["flush"] and n % 4 == 0 and n >= 4
+    assert calls["sync"] == n // 4
