@@ -450,6 +450,11 @@ def extra_measurements(args, g, u1, d1, pts, ref_pts, flush, stream):
 
     res = {}
     widths = {}
+    peak, _ = measured_peaks()
+
+    def step_frac(ms):
+        # the step against the spread+FFT memory model (STEP_BYTES_PER_SAMPLE)
+        return STEP_BYTES_PER_SAMPLE * n_src / (ms * 1e-3) / 1e9 / peak
     if "deterministic" in args.extras:
         # the atomic-free (bit-reproducible) spreading path on the same workload
         with FresnelPlan(g, d1, kernel_width=args.width, deterministic=True) as p:
@@ -468,7 +473,8 @@ def extra_measurements(args, g, u1, d1, pts, ref_pts, flush, stream):
                 ms = time_device_ms(lambda: p.execute(u1_d, out=out), steps, 3, flush, stream)
                 full, orc = accuracy(out)
             widths[str(w)] = {"samples_per_s": n_src / (ms * 1e-3), "ms": ms,
-                              "rel_l2_vs_es12": full, "rel_l2_vs_oracle": orc}
+                              "rel_l2_vs_es12": full, "rel_l2_vs_oracle": orc,
+                              "step_roofline_frac": step_frac(ms)}
         res["es_widths"] = widths
 
     if "learned" in args.extras:
@@ -485,6 +491,7 @@ def extra_measurements(args, g, u1, d1, pts, ref_pts, flush, stream):
         match = [w for w in sorted(widths, key=int) if widths[w]["rel_l2_vs_es12"] <= full]
         res["learned"] = {
             "kernel_width": 4, "samples_per_s": n_src / (ms * 1e-3), "ms": ms,
+            "step_roofline_frac": step_frac(ms),
             "rel_l2_vs_es12": full, "rel_l2_vs_oracle": orc,
             "target_rel_l2": 1e-4, "meets_target": orc <= 1e-4,
             "gain_vs_es4_error": widths["4"]["rel_l2_vs_es12"] / full if "4" in widths else None,
