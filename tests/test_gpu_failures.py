@@ -5,6 +5,8 @@ buffer left behind (asfd_debug_live_buffers), and the plan finally built must
 still match the oracle.  Nothing here makes a kernel fail."""
 from __future__ import annotations
 
+import gc
+
 import numpy as np
 import pytest
 
@@ -27,7 +29,11 @@ def lib():
 
 def build_with_failures(lib, make, limit=200):
     """Calls make() with 0, 1, 2, ... allocations allowed; returns the object
-    and the number of allocations it needed."""
+    and the number of allocations it needed.  Plans of earlier tests that
+    only the cycle collector would free are collected first, and collection
+    is paused meanwhile, so that the live-buffer count moves only with make()."""
+    gc.collect()
+    gc.disable()
     base = lib.asfd_debug_live_buffers()
     try:
         for k in range(limit):
@@ -41,12 +47,14 @@ def build_with_failures(lib, make, limit=200):
             return obj, k
     finally:
         lib.asfd_debug_fail_allocations(-1)
+        gc.enable()
     raise AssertionError("still failing after the allocation limit")
 
 
 @pytest.mark.parametrize("deterministic", [False, True])
 def test_plan_allocation_failures_leave_nothing_behind(lib, deterministic):
     g, u1, d1 = W.make("sinusoid64")
+    gc.collect()
     base = lib.asfd_debug_live_buffers()
     plan, needed = build_with_failures(lib, lambda: FresnelPlan(g, d1, deterministic=deterministic))
     assert needed > 0
@@ -64,6 +72,7 @@ def test_batch_allocation_failures_leave_nothing_behind(lib):
     rng = np.random.default_rng(71)
     u1b = (rng.standard_normal(u1.shape) + 1j * rng.standard_normal(u1.shape)).astype(np.complex64)
     items = [(g, u1, d1), (g, u1b, 0.5 * d1)]
+    gc.collect()
     base = lib.asfd_debug_live_buffers()
     batch, needed = build_with_failures(lib, lambda: FresnelBatch([(g, d1) for g, _, d1 in items]))
     assert needed > 0
