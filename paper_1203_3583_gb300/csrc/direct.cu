@@ -162,10 +162,12 @@ asfd_status direct_sum(const asfd_params* p, const double* d1, const float2* u1,
     for (double x : pos)
         if (!(std::isfinite(x) && x > 0.0))
             return fail(ASFD_ERR_ARG, "pitches, wavelength and z0 must be finite and > 0");
-    if (npts == 0) return ASFD_OK;
     if (!(std::isfinite(p->incidence_sx) && std::isfinite(p->incidence_sy) &&
           p->incidence_sx * p->incidence_sx + p->incidence_sy * p->incidence_sy < 1.0))
         return fail(ASFD_ERR_ARG, "incidence direction cosines need sx^2 + sy^2 < 1");
+    if (!(std::isfinite(p->offset_x) && std::isfinite(p->offset_y)))
+        return fail(ASFD_ERR_ARG, "source offsets must be finite");
+    if (npts == 0) return ASFD_OK;
     const double sz = std::sqrt(1.0 - p->incidence_sx * p->incidence_sx -
                                 p->incidence_sy * p->incidence_sy);
     DirectGeom g{p->n1x, p->n1y, p->m2x, p->m2y, p->p1x, p->p1y, p->p2x, p->p2y,

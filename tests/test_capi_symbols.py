@@ -97,3 +97,90 @@ def test_debug_hooks_without_gpu(lib_path):
     assert lib.asfd_debug_live_buffers() >= 0
     lib.asfd_debug_fail_allocations(2)
     lib.asfd_debug_fail_allocations(-1)
+
+
+def _status(lib, p):
+    import ctypes
+    out = ctypes.c_void_p()
+    rc = lib.asfd_plan_create(ctypes.byref(out), ctypes.byref(p), ctypes.c_void_p(1), None)
+    assert out.value is None
+    return rc
+
+
+def test_plan_parameter_checks_without_gpu(lib_path):
+    """Every asfd_params field with a rule is checked on the host, before any
+    device call, with ASFD_ERR_ARG (1) or ASFD_ERR_UNSUPPORTED (5)."""
+    from paper_1203_3583_gb300 import capi
+    lib = capi.load(lib_path)
+    g = dict(n1x=64, n1y=64, p1x=1e-5, p1y=1e-5, m2x=64, m2y=64, p2x=1e-5, p2y=1e-5,
+             lam=633e-9, z0=0.05)
+    cases = [
+        (capi.make_params(g, kernel_width=1), 5),
+        (capi.make_params(g, kind=7), 1),
+        (capi.make_params(g, kind=capi.ASFD_KERNEL_LEARNED, kernel_width=7), 5),
+        (capi.make_params(g, sigma=1.0), 5),
+        (capi.make_params(g, sigma=float("nan")), 1),
+        (capi.make_params(g, es_beta=-1.0), 1),
+        (capi.make_params(dict(g, sx=0.8, sy=0.7)), 1),          # grazing: sx^2 + sy^2 >= 1
+        (capi.make_params(dict(g, sx=float("nan"))), 1),
+        (capi.make_params(dict(g, ox=float("inf"))), 1),
+        (capi.make_params(dict(g, p2y=0.0)), 1),
+        (capi.make_params(dict(g, n1y=70000)), 1),
+        (capi.make_params(dict(g, m2x=16384)), 5),               # sigma * m2 above 16384
+    ]
+    for p, want in cases:
+        assert _status(lib, p) == want, (p, want, lib.asfd_last_error())
+    p = capi.make_params(g)
+    p.deterministic = 2
+    assert _status(lib, p) == 1
+
+
+def test_line_plan_parameter_checks_without_gpu(lib_path):
+    import ctypes
+    from paper_1203_3583_gb300 import capi
+    lib = capi.load(lib_path)
+    fake = ctypes.c_void_p(1)
+
+    def status(**kw):
+        base = dict(m2=1024, p2=1e-5, lam=633e-9, z0=1.0, sigma=2.0, kernel_width=7, es_beta=0.0,
+                    incidence_s=0.0)
+        base.update(kw)
+        p = capi.LineParams(**base)
+        out = ctypes.c_void_p()
+        rc = lib.asfd_line_plan_create(ctypes.byref(out), ctypes.byref(p), fake, fake, fake, 16, None)
+        assert out.value is None
+        return rc
+
+    assert status(m2=1023) == 1
+    assert status(p2=-1e-5) == 1
+    assert status(z0=float("inf")) == 1
+    assert status(incidence_s=1.0) == 1
+    assert status(kernel_width=1) == 5
+    assert status(sigma=1.5) == 5          # 1536 is not a power of two
+    assert status(es_beta=-2.0) == 1
+    out = ctypes.c_void_p()
+    p = capi.LineParams(1024, 1e-5, 633e-9, 1.0, 2.0, 7, 0.0, 0.0)
+    assert lib.asfd_line_plan_create(ctypes.byref(out), ctypes.byref(p), fake, fake, fake, 0,
+                                     None) == 1  # no samples
+
+
+def test_direct_sum_checks_without_gpu(lib_path):
+    """With no destination points the direct sum validates and returns without
+    touching the device."""
+    import ctypes
+    from paper_1203_3583_gb300 import capi
+    lib = capi.load(lib_path)
+    g = dict(n1x=64, n1y=64, p1x=1e-5, p1y=1e-5, m2x=64, m2y=64, p2x=1e-5, p2y=1e-5,
+             lam=633e-9, z0=0.05)
+    fake = ctypes.c_void_p(1)
+
+    def status(geom, form=7):
+        p = capi.make_params(geom)
+        return lib.asfd_direct_sum(ctypes.byref(p), fake, fake, form, 0, None, None, None, None)
+
+    assert status(g) == 0
+    assert status(g, form=4) == 1
+    assert status(dict(g, n1x=63)) == 1
+    assert status(dict(g, lam=0.0)) == 1
+    assert status(dict(g, sx=0.6, sy=0.9)) == 1
+    assert status(dict(g, oy=float("nan"))) == 1
