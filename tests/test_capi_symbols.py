@@ -184,3 +184,38 @@ def test_direct_sum_checks_without_gpu(lib_path):
     assert status(dict(g, lam=0.0)) == 1
     assert status(dict(g, sx=0.6, sy=0.9)) == 1
     assert status(dict(g, oy=float("nan"))) == 1
+
+
+def test_batch_multi_and_fft_checks_without_gpu(lib_path):
+    import ctypes
+    from paper_1203_3583_gb300 import capi
+    lib = capi.load(lib_path)
+    g = dict(n1x=64, n1y=64, p1x=1e-5, p1y=1e-5, m2x=64, m2y=64, p2x=1e-5, p2y=1e-5,
+             lam=633e-9, z0=0.05)
+    fake = ctypes.c_void_p(1)
+
+    def batch(params, count=None):
+        arr = (capi.Params * len(params))(*params)
+        d1s = (ctypes.c_void_p * len(params))(*([fake] * len(params)))
+        out = ctypes.c_void_p()
+        rc = lib.asfd_batch_create(ctypes.byref(out), arr, d1s,
+                                   len(params) if count is None else count, None)
+        assert out.value is None
+        return rc
+
+    p7 = capi.make_params(g)
+    assert batch([p7], count=0) == 1
+    assert batch([p7, capi.make_params(g, kernel_width=5)]) == 5        # mixed widths
+    assert batch([capi.make_params(g, kind=capi.ASFD_KERNEL_LEARNED, kernel_width=4)]) == 5
+    assert batch([capi.make_params(g, kernel_width=3)]) == 5            # batch widths 4..8
+    # multi-surface sums: empty or NULL inputs
+    plans = (ctypes.c_void_p * 1)(None)
+    u1s = (ctypes.c_void_p * 1)(fake)
+    assert lib.asfd_multi_execute(plans, u1s, 1, fake, None) == 1
+    assert lib.asfd_multi_execute(plans, u1s, 0, fake, None) == 1
+    # FFT lines: length, sign and buffers
+    assert lib.asfd_fft_lines(100, 1, -1, fake, fake, None) == 1
+    assert lib.asfd_fft_lines(32768, 1, -1, fake, fake, None) == 1
+    assert lib.asfd_fft_lines(64, 1, 0, fake, fake, None) == 1
+    assert lib.asfd_fft_lines(64, 1, -1, None, fake, None) == 1
+    assert lib.asfd_fft_lines(64, -1, -1, fake, fake, None) == 1
