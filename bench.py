@@ -36,7 +36,7 @@ WORKLOAD = "smooth_random2048"
 FALLBACK_HBM_GBS = 6800.0
 # seconds of untimed back-to-back steps under clock sampling before the timed region
 CLOCK_LOAD_S = 0.5
-# extra lines after the headline (each on the same single-GPU machine)
+# extra lines after the headline (each on the same single GPU)
 EXTRAS = ("deterministic", "es_widths", "learned", "direct_sum", "line", "multi", "adjoint", "batch",
           "fft_reference")
 
@@ -182,7 +182,10 @@ def measured_peaks():
 
 
 def stage_bytes(info, g):
-    """Algorithmic HBM bytes per launch of each stage."""
+    """Algorithmic HBM bytes per launch of each stage: the spread reads u1 and
+    q (12 B per sample) plus the axis tables and writes the band of the fine
+    grid once; the row pass reads the band and writes band rows x m2x; the
+    column pass reads those and writes u2 plus the destination tables."""
     n = g["n1x"] * g["n1y"]
     band_rows = info["band_y1"] - info["band_y0"]
     band_cols = info["band_x1"] - info["band_x0"]

@@ -28,8 +28,10 @@
  *    asynchronous calls, until the work queued on `stream` completes).
  *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
  *    stream).  Device work is queued asynchronously on it unless stated.
- *  - A plan owns its device tables and work buffers.  Calls on one plan must
- *    not overlap in time (one stream at a time).
+ *  - A plan owns its device tables; its work buffers are its own (allocated
+ *    on first use) or carved from a caller-owned workspace
+ *    (asfd_set_workspace).  Calls on one plan must not overlap in time (one
+ *    stream at a time).
  *  - No exceptions cross the ABI.  Every call returns an asfd_status; a
  *    one-line description of the last failure on the calling thread is
  *    available from asfd_last_error().
@@ -120,7 +122,8 @@ typedef struct {
  * Errors: ASFD_ERR_ARG for invalid sizes/pitches, non-finite d1, d1 >= z0;
  * ASFD_ERR_UNSUPPORTED when max |d1|/z0 > 0.1 or a size is out of range;
  * ASFD_ERR_NOMEM / ASFD_ERR_CUDA on allocation or launch failure.
- * On failure *out is set to NULL and nothing is leaked.
+ * On failure *out is set to NULL and nothing is leaked.  The work buffers
+ * (fine grid and row buffer) are not allocated here: see asfd_set_workspace.
  */
 asfd_status asfd_plan_create(asfd_plan* out, const asfd_params* p, const double* d1_dev,
                              void* stream);
@@ -131,19 +134,57 @@ asfd_status asfd_plan_create(asfd_plan* out, const asfd_params* p, const double*
 asfd_status asfd_plan_update_d1(asfd_plan plan, const double* d1_dev, void* stream);
 
 /*
+ * Caller-owned work memory.  A plan holds two kinds of device memory: its
+ * tables (O(n1x + n1y + m2x + m2y) plus O(tiles); built by asfd_plan_create)
+ * and its work buffers, whose sizes scale with the grids of the NUFFT that
+ * evaluates Eq. 8 (Sec. 2): the sigma-oversampled fine grid
+ * (sigma m2x x sigma m2y complex), the row-FFT output (sigma m2y x m2x
+ * complex), the staging of u1 and u2 for asfd_execute_host, and for learned
+ * plans the training output and residual (m2x x m2y complex each).
+ *
+ * asfd_workspace_bytes(p): bytes of a workspace holding every work buffer of
+ * a plan with parameters p (each region 256-byte aligned); 0 if p is invalid
+ * (asfd_last_error() says why).  Touches no device.
+ *
+ * asfd_set_workspace(plan, ws_dev, bytes): from now on the plan carves all of
+ * its work buffers from ws_dev (device memory of the plan's device, 256-byte
+ * aligned, bytes >= asfd_workspace_bytes of the plan's parameters), which the
+ * caller owns (e.g. a tensor of PyTorch's caching allocator) and must keep
+ * alive, and not use otherwise, while calls on the plan can run.  Work
+ * buffers the plan had allocated itself are freed.  With a workspace set, no
+ * call on the plan allocates device memory.  ws_dev = NULL with bytes = 0
+ * detaches the workspace; the plan then allocates its own work buffers again
+ * on first use.  Without a workspace a plan allocates its work buffers at the
+ * first call that needs them (asfd_execute, asfd_execute_stage,
+ * asfd_execute_host, asfd_adjoint, the learned training calls, and
+ * asfd_multi_execute for its first plan): make one such call, or set a
+ * workspace, before capturing calls into a CUDA graph.  Synchronises the
+ * device (work queued on the old buffers must finish).  Several plans may
+ * share one workspace only if their calls never overlap in time.
+ * Errors: ASFD_ERR_ARG (NULL plan, too small, misaligned, not device memory
+ * of the plan's device, NULL with bytes != 0), ASFD_ERR_CUDA.
+ */
+size_t asfd_workspace_bytes(const asfd_params* p);
+asfd_status asfd_set_workspace(asfd_plan plan, void* ws_dev, size_t bytes);
+
+/*
  * Forward transform, Eq. 8: u2 = outer(x2) * NUFT[u_I u1 exp(ik(-d1 + |x1|^2/(2 r0)))].
  * u1_dev: device [n1y][n1x] complex; u2_dev: device [m2y][m2x] complex.
  * Stages (all CUDA kernels on `stream`): per-sample prefactor fused into the
  * tiled spread onto the sigma-oversampled grid, row FFT with crop, column FFT
  * fused with kernel deconvolution, crop and the destination chirp.
- * Asynchronous.  Errors: ASFD_ERR_ARG (NULL), ASFD_ERR_CUDA (launch).
+ * Asynchronous (the first call without a workspace allocates the plan's work
+ * buffers).  Errors: ASFD_ERR_ARG (NULL), ASFD_ERR_NOMEM (work buffers),
+ * ASFD_ERR_CUDA (launch).
  */
 asfd_status asfd_execute(asfd_plan plan, const float* u1_dev, float* u2_dev, void* stream);
 
 /*
  * Same transform on HOST buffers: copies u1 host->device, runs asfd_execute,
  * copies u2 device->host, and synchronises `stream` before returning.
- * u1_host: [n1y][n1x] complex; u2_host: [m2y][m2x] complex.
+ * u1_host: [n1y][n1x] complex; u2_host: [m2y][m2x] complex.  The device
+ * copies of u1 and u2 are work buffers of the plan (see asfd_set_workspace).
+ * Errors: ASFD_ERR_ARG, ASFD_ERR_NOMEM (work buffers), ASFD_ERR_CUDA.
  */
 asfd_status asfd_execute_host(asfd_plan plan, const float* u1_host, float* u2_host, void* stream);
 
@@ -420,9 +461,10 @@ asfd_status asfd_fft_lines(int n, int lines, int sign, const float* in_dev, floa
  *   n: power of two in [16, 16384]; larger n is rejected with ASFD_ERR_ARG
  *      and a message naming the limit.  Other arguments and the result are
  *      exactly as for asfd_fft_lines.
- * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  Every call on a device shares the one array
+ * Every call looks up the array's device address (cudaGetSymbolAddress) on
+ * the current device, so a device reset between calls is harmless; the first
+ * call on a device also loads the library's module there, so make that first
+ * call before any stream capture.  Every call on a device shares the one array
  * and rewrites the n entries it reads before its transform, so calls that
  * can overlap on the GPU (different streams, or different host threads on
  * one device) race on the table and must be serialised by the caller.

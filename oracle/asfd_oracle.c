@@ -23,7 +23,7 @@
  * exp(-ik d1) factor of Eq. 5 separately, as written, and accumulates every
  * term in FP64 with no table, no kernel and no FFT.
  *
- * Readings where the paper is garbled or silent (all listed in the design doc):
+ * Readings where the paper is garbled or silent:
  *  - cross-term sign: Eq. 7 prints "+ik x1.x2/(z0-d1)"; Eqs. 4 and 5 and the
  *    NUFT definition (Eq. 9) carry a minus sign.  The minus sign is used.
  *  - quadrature weight of the integral over x1: the projected area element

@@ -102,6 +102,8 @@ SIGNATURES = {
     "asfd_batch_destroy": (_int, [_vp]),
     "asfd_plan_create": (_int, [ctypes.POINTER(_vp), ctypes.POINTER(Params), _vp, _vp]),
     "asfd_plan_update_d1": (_int, [_vp, _vp, _vp]),
+    "asfd_workspace_bytes": (ctypes.c_size_t, [ctypes.POINTER(Params)]),
+    "asfd_set_workspace": (_int, [_vp, _vp, ctypes.c_size_t]),
     "asfd_execute": (_int, [_vp, _vp, _vp, _vp]),
     "asfd_execute_host": (_int, [_vp, _vp, _vp, _vp]),
     "asfd_execute_stage": (_int, [_vp, _int, _vp, _vp, _vp]),
@@ -262,6 +264,26 @@ def asfd_plan_update_d1(plan, d1: torch.Tensor, n1x: int, n1y: int, stream=None)
     lib = load()
     _check(lib.asfd_plan_update_d1(plan, _dev_ptr(d1, torch.float64, (n1y, n1x), "d1"),
                                    _stream(stream)))
+
+
+def asfd_workspace_bytes(params: Params) -> int:
+    """Bytes of a workspace holding every work buffer of a plan (0 if invalid)."""
+    n = int(load().asfd_workspace_bytes(ctypes.byref(params)))
+    if n == 0:
+        raise AsfdError(ASFD_ERR_ARG, load().asfd_last_error().decode())
+    return n
+
+
+def asfd_set_workspace(plan, ws: torch.Tensor | None) -> None:
+    """Hands the plan a caller-owned workspace (a CUDA uint8 tensor of at
+    least asfd_workspace_bytes() bytes), or detaches it with ws=None."""
+    if ws is None:
+        _check(load().asfd_set_workspace(plan, None, 0))
+        return
+    if not (isinstance(ws, torch.Tensor) and ws.is_cuda and ws.dtype == torch.uint8
+            and ws.is_contiguous()):
+        raise TypeError("workspace must be a contiguous uint8 CUDA tensor")
+    _check(load().asfd_set_workspace(plan, ctypes.c_void_p(ws.data_ptr()), ws.numel()))
 
 
 def asfd_execute(plan, u1: torch.Tensor, u2: torch.Tensor, shape1, shape2, stream=None) -> None:

@@ -121,9 +121,12 @@ struct asfd_plan_s {
     long long tile_pairs = 0;
     size_t tile_src_cap = 0;
 
-    // work buffers
+    // work buffers: allocated by the plan on first use, or carved from a
+    // caller-owned workspace (asfd_set_workspace)
     float2* grid = nullptr;         // [nfy][nfx]
     float2* rows = nullptr;         // [nfy][m2x] row-FFT output (band rows first)
+    char* ws = nullptr;             // caller-owned workspace, or NULL
+    size_t ws_bytes = 0;
     unsigned* status = nullptr;     // device status word
     // learned kernel (kind == ASFD_KERNEL_LEARNED)
     bool learned = false;
@@ -140,10 +143,10 @@ struct asfd_plan_s {
     float2* cyb = nullptr;
     float* lcorr = nullptr;         // [m2x + m2y] current deconvolution corrections
     float* lcgrad = nullptr;        // [m2x + m2y] dL/dcorrection
-    float2* lu2 = nullptr;          // [m2y][m2x] training forward output
-    float2* lres = nullptr;         // [m2y][m2x] loss gradient
+    float2* lu2 = nullptr;          // [m2y][m2x] training forward output (work buffer)
+    float2* lres = nullptr;         // [m2y][m2x] loss gradient (work buffer)
     double* lred = nullptr;         // [2] loss reductions
-    float2* stage_u1 = nullptr;     // staging for asfd_execute_host (allocated on first use)
+    float2* stage_u1 = nullptr;     // staging for asfd_execute_host (work buffer)
     float2* stage_u2 = nullptr;
 
     std::vector<asfd::DevBuf> owned;
@@ -208,6 +211,22 @@ asfd_status build_twiddles(float2* tw, int L, cudaStream_t st);
 asfd_status plan_build_tables(asfd_plan_s* P, cudaStream_t st);
 asfd_status plan_build_d1(asfd_plan_s* P, const double* d1, cudaStream_t st);
 asfd_status plan_alloc_buffer(asfd_plan_s* P, void** p, size_t bytes);
+
+// Work buffers (sizes scale with the grids; everything else a plan holds is
+// a table).  Byte offsets of each inside a workspace, 256-byte aligned:
+// fine grid, row buffer, the host-execute staging of u1 and u2, and for
+// learned plans the training output and residual.
+struct WorkLayout {
+    size_t grid = 0, rows = 0, stage_u1 = 0, stage_u2 = 0, lu2 = 0, lres = 0, total = 0;
+};
+WorkLayout work_layout(const asfd_params& p, int nfx, int nfy);
+enum WorkNeed : unsigned { kWorkTransform = 1u, kWorkStaging = 2u, kWorkTraining = 4u };
+// Makes the work buffers in `need` available: carved from the workspace when
+// one is set, else allocated by the plan (once).
+asfd_status plan_ensure_work(asfd_plan_s* P, unsigned need);
+// Attaches a caller-owned workspace (releasing the plan's own work buffers)
+// or, with ws == NULL, detaches it.
+asfd_status plan_set_workspace(asfd_plan_s* P, void* ws, size_t bytes);
 // learned kernel
 asfd_status learned_init(asfd_plan_s* P, cudaStream_t st);
 asfd_status learned_refresh(asfd_plan_s* P, cudaStream_t st);   // features -> tables, deconvolution

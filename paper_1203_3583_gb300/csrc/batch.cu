@@ -324,6 +324,9 @@ asfd_status asfd_batch_create(asfd_batch* out, const asfd_params* params,
             B->plans.push_back(p);
             if (p->nfx > kBatchMaxNf || p->nfy > kBatchMaxNf)
                 return fail(ASFD_ERR_UNSUPPORTED, "batched fine grids are limited to 4096");
+            // the launch's argument table holds the plan's work buffers
+            r = plan_ensure_work(p, kWorkTransform);
+            if (r != ASFD_OK) return r;
         }
         ASFD_CUDA(cudaMallocHost(&B->host, sizeof(BatchSurf) * count));
         ASFD_CUDA(cudaMalloc(&B->dev, sizeof(BatchSurf) * count));

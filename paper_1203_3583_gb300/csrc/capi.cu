@@ -137,7 +137,9 @@ asfd_status asfd_execute(asfd_plan P, const float* u1_dev, float* u2_dev, void* 
     if (!P || !u1_dev || !u2_dev) return fail(ASFD_ERR_ARG, "plan, u1 or u2 is NULL");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     return on_device(P->device, [&]() -> asfd_status {
-        asfd_status s = launch_spread(P, reinterpret_cast<const float2*>(u1_dev), st);
+        asfd_status s = plan_ensure_work(P, kWorkTransform);
+        if (s != ASFD_OK) return s;
+        s = launch_spread(P, reinterpret_cast<const float2*>(u1_dev), st);
         if (s != ASFD_OK) return s;
         s = launch_fft_rows(P, st);
         if (s != ASFD_OK) return s;
@@ -155,6 +157,8 @@ asfd_status asfd_execute_stage(asfd_plan P, int stage, const float* u1_dev, floa
     if (stage < 0 || stage > 2) return fail(ASFD_ERR_ARG, "stage must be 0, 1 or 2");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     return on_device(P->device, [&]() -> asfd_status {
+        const asfd_status s = plan_ensure_work(P, kWorkTransform);
+        if (s != ASFD_OK) return s;
         if (stage == 0) return launch_spread(P, reinterpret_cast<const float2*>(u1_dev), st);
         if (stage == 1) return launch_fft_rows(P, st);
         return launch_fft_cols(P, reinterpret_cast<float2*>(u2_dev), st);
@@ -170,7 +174,9 @@ asfd_status asfd_adjoint(asfd_plan P, const float* u1_dev, const float* grad_u2_
     if (!grad_u1_dev && !grad_d1_dev) return ASFD_OK;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     return on_device(P->device, [&]() -> asfd_status {
-        asfd_status s = launch_fft_cols_adj(P, reinterpret_cast<const float2*>(grad_u2_dev), st);
+        asfd_status s = plan_ensure_work(P, kWorkTransform);
+        if (s != ASFD_OK) return s;
+        s = launch_fft_cols_adj(P, reinterpret_cast<const float2*>(grad_u2_dev), st);
         if (s != ASFD_OK) return s;
         s = launch_fft_rows_adj(P, st);
         if (s != ASFD_OK) return s;
@@ -185,26 +191,14 @@ asfd_status asfd_execute_host(asfd_plan P, const float* u1_host, float* u2_host,
     if (!P || !u1_host || !u2_host) return fail(ASFD_ERR_ARG, "plan, u1 or u2 is NULL");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     return on_device(P->device, [&]() -> asfd_status {
-        // staging buffers live for the plan's lifetime (allocated on first use)
+        // staging buffers: work buffers of the plan (its own, allocated on
+        // first use, or carved from the caller's workspace)
         const size_t b1 = sizeof(float2) * (size_t)P->prm.n1x * P->prm.n1y;
         const size_t b2 = sizeof(float2) * (size_t)P->prm.m2x * P->prm.m2y;
-        if (!P->stage_u1) {
-            void* a = nullptr;
-            void* b = nullptr;
-            if (cudaMalloc(&a, b1) != cudaSuccess || cudaMalloc(&b, b2) != cudaSuccess) {
-                cudaGetLastError();
-                if (a) cudaFree(a);
-                return fail(ASFD_ERR_NOMEM, "staging buffers for asfd_execute_host");
-            }
-            P->stage_u1 = static_cast<float2*>(a);
-            P->stage_u2 = static_cast<float2*>(b);
-            P->owned.push_back(DevBuf{a, b1});
-            P->owned.push_back(DevBuf{b, b2});
-            P->device_bytes += b1 + b2;
-            g_live_buffers += 2;
-        }
+        asfd_status s = plan_ensure_work(P, kWorkTransform | kWorkStaging);
+        if (s != ASFD_OK) return s;
         ASFD_CUDA(cudaMemcpyAsync(P->stage_u1, u1_host, b1, cudaMemcpyHostToDevice, st));
-        asfd_status s = launch_spread(P, P->stage_u1, st);
+        s = launch_spread(P, P->stage_u1, st);
         if (s != ASFD_OK) return s;
         s = launch_fft_rows(P, st);
         if (s != ASFD_OK) return s;
@@ -256,6 +250,22 @@ asfd_status asfd_check_device_status(asfd_plan P, void* stream)
         if (h & kStatusIndex) return fail(ASFD_ERR_STATE, "a device index check failed");
         return fail(ASFD_ERR_ARG, "device status word " + std::to_string(h));
     });
+}
+
+size_t asfd_workspace_bytes(const asfd_params* p)
+{
+    clear_error();
+    int nfx = 0, nfy = 0;
+    double beta = 0.0;
+    if (plan_validate(p, &nfx, &nfy, &beta) != ASFD_OK) return 0;
+    return work_layout(*p, nfx, nfy).total;
+}
+
+asfd_status asfd_set_workspace(asfd_plan P, void* ws_dev, size_t bytes)
+{
+    clear_error();
+    if (!P) return fail(ASFD_ERR_ARG, "plan is NULL");
+    return on_device(P->device, [&] { return plan_set_workspace(P, ws_dev, bytes); });
 }
 
 asfd_status asfd_destroy(asfd_plan P)
@@ -317,6 +327,8 @@ asfd_status asfd_learned_train_step(asfd_plan P, const float* u1_dev, const floa
     if (!(lr >= 0.f) || !std::isfinite(lr)) return fail(ASFD_ERR_ARG, "lr must be finite and >= 0");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     return on_device(P->device, [&]() -> asfd_status {
+        const asfd_status s = plan_ensure_work(P, kWorkTransform | kWorkTraining);
+        if (s != ASFD_OK) return s;
         return learned_train_step(P, reinterpret_cast<const float2*>(u1_dev),
                                   reinterpret_cast<const float2*>(ref_u2_dev), lr, loss_host, st);
     });
@@ -331,7 +343,9 @@ asfd_status asfd_learned_gradient(asfd_plan P, const float* u1_dev, const float*
     if (count != (size_t)kLearnParams) return fail(ASFD_ERR_ARG, "count must equal asfd_learned_param_count()");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     return on_device(P->device, [&]() -> asfd_status {
-        asfd_status s = learned_gradient(P, reinterpret_cast<const float2*>(u1_dev),
+        asfd_status s = plan_ensure_work(P, kWorkTransform | kWorkTraining);
+        if (s != ASFD_OK) return s;
+        s = learned_gradient(P, reinterpret_cast<const float2*>(u1_dev),
                                          reinterpret_cast<const float2*>(ref_u2_dev), st);
         if (s != ASFD_OK) return s;
         ASFD_CUDA(cudaMemcpyAsync(grad_host, P->lgrad, sizeof(float) * kLearnParams,
@@ -350,7 +364,9 @@ asfd_status asfd_multi_execute(const asfd_plan* plans, const float* const* u1_de
         return fail(ASFD_ERR_ARG, "plans, u1 array and u2 must be non-NULL, count >= 1");
     for (int i = 0; i < count; ++i)
         if (!plans[i]) return fail(ASFD_ERR_ARG, "plan is NULL");
-    return on_device(plans[0]->device, [&] {
+    return on_device(plans[0]->device, [&]() -> asfd_status {
+        const asfd_status s = plan_ensure_work(plans[0], kWorkTransform);
+        if (s != ASFD_OK) return s;
         return multi_execute(plans, reinterpret_cast<const float2* const*>(u1_devs), count,
                              reinterpret_cast<float2*>(u2_dev), static_cast<cudaStream_t>(stream));
     });

@@ -463,7 +463,6 @@ asfd_status learned_refresh(asfd_plan_s* P, cudaStream_t st)
 asfd_status learned_init(asfd_plan_s* P, cudaStream_t st)
 {
     const int nst = P->nstx * P->nsty;
-    const size_t m1 = (size_t)P->prm.m2x * P->prm.m2y;
     const int mm = P->prm.m2x + P->prm.m2y;
     auto A = [&](void** p, size_t bytes) { return plan_alloc_buffer(P, p, bytes); };
     asfd_status s;
@@ -480,8 +479,6 @@ asfd_status learned_init(asfd_plan_s* P, cudaStream_t st)
     LA(cyb, sizeof(float2) * P->prm.m2y);
     LA(lcorr, sizeof(float) * mm);
     LA(lcgrad, sizeof(float) * mm);
-    LA(lu2, sizeof(float2) * m1);
-    LA(lres, sizeof(float2) * m1);
     LA(lred, sizeof(double) * 2);
 #undef LA
     // the ES width-4 deconvolution/chirp tables become the base tables

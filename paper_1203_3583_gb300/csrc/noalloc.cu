@@ -9,7 +9,6 @@
 // them, asfd_fft_lines_noalloc keeps the table in a fixed array compiled into
 // this library instead (kStaticFftMaxLength complex values, 128 KiB per GPU
 // that loads the library, held until the process exits).
-#include <mutex>
 #include <string>
 
 #include "asfd_impl.cuh"
@@ -22,40 +21,20 @@ asfd_status launch_fft_lines_tw(int n, int lines, int sign, const float2* in, fl
 namespace {
 
 constexpr int kStaticFftMaxLength = 16384;
-constexpr int kMaxDevices = 64;
 
 // Twiddle scratch shared by every call on a device.  Host code must not use
 // the symbol itself as a pointer: its device address comes from
 // cudaGetSymbolAddress below.
 static __device__ __align__(256) float2 g_fft_twiddle_scratch[kStaticFftMaxLength];
 
-std::mutex g_mu;
-float2* g_scratch_addr[kMaxDevices] = {};
-
-__global__ void static_twiddle_kernel(float2* tw, int n)
-{
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= n) return;
-    double s, c;
-    sincospi(2.0 * (double)k / (double)n, &s, &c);
-    tw[k] = make_float2((float)c, (float)-s);
-}
-
-// Device address of the scratch array on the current device, looked up
-// once per device.
+// Device address of the scratch array on the current device.  Looked up on
+// every call (cudaGetSymbolAddress allocates nothing and is cheap), so a call
+// after the device's context was reset and re-created uses the new address.
 asfd_status scratch_address(float2** out)
 {
-    int dev = 0;
-    ASFD_CUDA(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= kMaxDevices)
-        return fail(ASFD_ERR_UNSUPPORTED, "device ordinal above " + std::to_string(kMaxDevices - 1));
-    std::lock_guard<std::mutex> g(g_mu);
-    if (!g_scratch_addr[dev]) {
-        void* p = nullptr;
-        ASFD_CUDA(cudaGetSymbolAddress(&p, g_fft_twiddle_scratch));
-        g_scratch_addr[dev] = static_cast<float2*>(p);
-    }
-    *out = g_scratch_addr[dev];
+    void* p = nullptr;
+    ASFD_CUDA(cudaGetSymbolAddress(&p, g_fft_twiddle_scratch));
+    *out = static_cast<float2*>(p);
     return ASFD_OK;
 }
 
@@ -81,9 +60,10 @@ extern "C" asfd_status asfd_fft_lines_noalloc(int n, int lines, int sign, const 
     if (s != ASFD_OK) return s;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     // the table of the previous call may be for another length: rewrite all n
-    // entries the transform reads, on the same stream, before it runs
-    static_twiddle_kernel<<<(n + 255) / 256, 256, 0, st>>>(tw, n);
-    ASFD_CUDA(cudaGetLastError());
+    // entries the transform reads, on the same stream, before it runs (the
+    // generator is the one asfd_fft_lines uses for its own tables)
+    s = build_twiddles(tw, n, st);
+    if (s != ASFD_OK) return s;
     return launch_fft_lines_tw(n, lines, sign, reinterpret_cast<const float2*>(in_dev),
                                reinterpret_cast<float2*>(out_dev), tw, st);
 }

@@ -430,10 +430,105 @@ asfd_status plan_alloc(asfd_plan_s* P)
     A(col_range, p.n1x);
     A(row_range, p.n1y);
     A(step_min, kStepBlocks);
-    A(grid, (size_t)P->nfx * P->nfy);
-    A(rows, (size_t)P->nfy * p.m2x);
     A(status, 2);
 #undef A
+    return ASFD_OK;
+}
+
+WorkLayout work_layout(const asfd_params& p, int nfx, int nfy)
+{
+    const auto up = [](size_t b) { return (b + 255) / 256 * 256; };
+    const size_t c = sizeof(float2);
+    WorkLayout L;
+    size_t o = 0;
+    L.grid = o;
+    o += up(c * (size_t)nfx * nfy);
+    L.rows = o;
+    o += up(c * (size_t)nfy * p.m2x);
+    L.stage_u1 = o;
+    o += up(c * (size_t)p.n1x * p.n1y);
+    L.stage_u2 = o;
+    o += up(c * (size_t)p.m2x * p.m2y);
+    if (p.kind == ASFD_KERNEL_LEARNED) {
+        L.lu2 = o;
+        o += up(c * (size_t)p.m2x * p.m2y);
+        L.lres = o;
+        o += up(c * (size_t)p.m2x * p.m2y);
+    }
+    L.total = o;
+    return L;
+}
+
+asfd_status plan_ensure_work(asfd_plan_s* P, unsigned need)
+{
+    if (P->ws) return ASFD_OK;  // every work buffer was carved when the workspace was set
+    const asfd_params& p = P->prm;
+    asfd_status s;
+    if ((need & kWorkTransform) && !P->grid) {
+        if ((s = alloc_n(P, &P->grid, (size_t)P->nfx * P->nfy)) != ASFD_OK) return s;
+        if ((s = alloc_n(P, &P->rows, (size_t)P->nfy * p.m2x)) != ASFD_OK) {
+            release(P, P->grid);
+            P->grid = nullptr;
+            return s;
+        }
+    }
+    if ((need & kWorkStaging) && !P->stage_u1) {
+        if ((s = alloc_n(P, &P->stage_u1, (size_t)p.n1x * p.n1y)) != ASFD_OK) return s;
+        if ((s = alloc_n(P, &P->stage_u2, (size_t)p.m2x * p.m2y)) != ASFD_OK) {
+            release(P, P->stage_u1);
+            P->stage_u1 = nullptr;
+            return s;
+        }
+    }
+    if ((need & kWorkTraining) && P->learned && !P->lu2) {
+        if ((s = alloc_n(P, &P->lu2, (size_t)p.m2x * p.m2y)) != ASFD_OK) return s;
+        if ((s = alloc_n(P, &P->lres, (size_t)p.m2x * p.m2y)) != ASFD_OK) {
+            release(P, P->lu2);
+            P->lu2 = nullptr;
+            return s;
+        }
+    }
+    return ASFD_OK;
+}
+
+asfd_status plan_set_workspace(asfd_plan_s* P, void* ws, size_t bytes)
+{
+    const WorkLayout L = work_layout(P->prm, P->nfx, P->nfy);
+    if (ws) {
+        if (bytes < L.total)
+            return fail(ASFD_ERR_ARG, "workspace of " + std::to_string(bytes) +
+                                          " bytes is smaller than asfd_workspace_bytes() = " +
+                                          std::to_string(L.total));
+        if (reinterpret_cast<uintptr_t>(ws) % 256 != 0)
+            return fail(ASFD_ERR_ARG, "workspace must be 256-byte aligned");
+        cudaPointerAttributes at{};
+        ASFD_CUDA(cudaPointerGetAttributes(&at, ws));
+        if ((at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged) ||
+            at.device != P->device)
+            return fail(ASFD_ERR_ARG, "workspace must be device memory of the plan's device");
+    } else if (bytes != 0) {
+        return fail(ASFD_ERR_ARG, "a NULL workspace must come with bytes = 0");
+    }
+    // queued work may still use the buffers being replaced
+    ASFD_CUDA(cudaDeviceSynchronize());
+    float2** bufs[] = {&P->grid, &P->rows, &P->stage_u1, &P->stage_u2, &P->lu2, &P->lres};
+    for (float2** b : bufs) {
+        if (*b && !P->ws) release(P, *b);
+        *b = nullptr;
+    }
+    P->ws = static_cast<char*>(ws);
+    P->ws_bytes = ws ? bytes : 0;
+    if (ws) {
+        char* base = P->ws;
+        P->grid = reinterpret_cast<float2*>(base + L.grid);
+        P->rows = reinterpret_cast<float2*>(base + L.rows);
+        P->stage_u1 = reinterpret_cast<float2*>(base + L.stage_u1);
+        P->stage_u2 = reinterpret_cast<float2*>(base + L.stage_u2);
+        if (P->learned) {
+            P->lu2 = reinterpret_cast<float2*>(base + L.lu2);
+            P->lres = reinterpret_cast<float2*>(base + L.lres);
+        }
+    }
     return ASFD_OK;
 }
 

@@ -28,7 +28,11 @@ class FresnelPlan:
 
     def __init__(self, geometry: dict, d1, sigma: float = 2.0, kernel_width: int = 7,
                  es_beta: float = 0.0, stream=None, kind: str = "es",
-                 deterministic: bool = False):
+                 deterministic: bool = False, workspace: bool = False):
+        """workspace=True: the plan's work buffers (fine grid, row buffer,
+        host-execute staging, learned training buffers) come from one uint8
+        tensor of PyTorch's caching allocator (asfd_set_workspace), so the
+        library allocates only the plan's tables."""
         self.geometry = dict(geometry)
         if kind not in ("es", "learned"):
             raise ValueError("kind must be 'es' or 'learned'")
@@ -42,7 +46,17 @@ class FresnelPlan:
         self.shape1 = (int(geometry["n1y"]), int(geometry["n1x"]))
         self.shape2 = (int(geometry["m2y"]), int(geometry["m2x"]))
         self._handle = None
+        self.workspace = None
         self._handle = capi.asfd_plan_create(self.params, _as_cuda_f64(d1), stream)
+        if workspace:
+            self.set_workspace(torch.empty(capi.asfd_workspace_bytes(self.params),
+                                           dtype=torch.uint8, device="cuda"))
+
+    def set_workspace(self, ws: torch.Tensor | None) -> None:
+        """Attach a caller-owned workspace (uint8 CUDA tensor; kept alive by
+        this object) or detach it (None)."""
+        capi.asfd_set_workspace(self.handle, ws)
+        self.workspace = ws
 
     @property
     def handle(self):
@@ -92,6 +106,7 @@ class FresnelPlan:
         if self._handle is not None:
             capi.asfd_destroy(self._handle)
             self._handle = None
+        self.workspace = None
 
     def __enter__(self):
         return self

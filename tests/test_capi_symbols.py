@@ -219,3 +219,30 @@ def test_batch_multi_and_fft_checks_without_gpu(lib_path):
     assert lib.asfd_fft_lines(64, 1, 0, fake, fake, None) == 1
     assert lib.asfd_fft_lines(64, 1, -1, None, fake, None) == 1
     assert lib.asfd_fft_lines(64, -1, -1, fake, fake, None) == 1
+
+
+def test_workspace_bytes_without_gpu(lib_path):
+    """asfd_workspace_bytes touches no device: its value is the sum of the
+    work buffers' sizes (fine grid sigma m2x x sigma m2y, row buffer
+    sigma m2y x m2x, staging n1x n1y + m2x m2y, plus 2 m2x m2y for learned
+    plans; complex64, each rounded up to 256 bytes), and 0 for invalid
+    parameters."""
+    from paper_1203_3583_gb300 import capi
+    lib = capi.load(lib_path)
+    up = lambda b: (b + 255) // 256 * 256  # noqa: E731
+    g = dict(n1x=2048, n1y=1000, p1x=4e-6, p1y=4e-6, m2x=1024, m2y=512, p2x=4e-6, p2y=4e-6,
+             lam=633e-9, z0=0.1)
+    p = capi.make_params(g)
+    nfx, nfy = 2048, 1024
+    want = up(8 * nfx * nfy) + up(8 * nfy * 1024) + up(8 * 2048 * 1000) + up(8 * 1024 * 512)
+    assert lib.asfd_workspace_bytes(p) == want
+    pl = capi.make_params(g, kernel_width=4, kind=capi.ASFD_KERNEL_LEARNED)
+    assert lib.asfd_workspace_bytes(pl) == want + 2 * up(8 * 1024 * 512)
+    # ragged sizes: every region still starts on a 256-byte boundary
+    g2 = dict(g, n1x=34, n1y=18, m2x=32, m2y=32)
+    assert lib.asfd_workspace_bytes(capi.make_params(g2)) == (
+        up(8 * 64 * 64) + up(8 * 64 * 32) + up(8 * 34 * 18) + up(8 * 32 * 32))
+    assert lib.asfd_workspace_bytes(capi.make_params(dict(g, n1x=63))) == 0
+    assert b"even" in lib.asfd_last_error()
+    assert lib.asfd_workspace_bytes(None) == 0
+    assert lib.asfd_set_workspace(None, None, 0) == 1

@@ -89,3 +89,46 @@ def test_hook_off_by_default(lib):
     g, u1, d1 = W.make("sinusoid64")
     with FresnelPlan(g, d1):
         pass
+
+
+def test_work_buffer_allocation_failures(lib):
+    """The work buffers a plan allocates on first use (fine grid and row
+    buffer at the first execution, the u1/u2 staging at the first
+    asfd_execute_host) go through the same hook: each refusal returns
+    ASFD_ERR_NOMEM, leaves no buffer behind and leaves the plan usable."""
+    g, u1, d1 = W.make("sinusoid64")
+    gc.collect()
+    base = lib.asfd_debug_live_buffers()
+    u1_t = torch.as_tensor(u1, device="cuda")
+    host_in = torch.as_tensor(u1).pin_memory()
+    host_out = torch.empty((g["m2y"], g["m2x"]), dtype=torch.complex64).pin_memory()
+    ref = oracle.eq7(g, u1, d1)
+    with FresnelPlan(g, d1) as plan:
+        tables = lib.asfd_debug_live_buffers()
+        for k in (0, 1):  # refuse the fine grid, then the row buffer
+            lib.asfd_debug_fail_allocations(k)
+            try:
+                with pytest.raises(capi.AsfdError) as ei:
+                    plan.execute(u1_t)
+            finally:
+                lib.asfd_debug_fail_allocations(-1)
+            assert ei.value.status == capi.ASFD_ERR_NOMEM
+            assert lib.asfd_debug_live_buffers() == tables
+        # refuse the grid, the row buffer, then (with those two in place) the
+        # staging of u1, then the staging of u2
+        for k, kept in ((0, 0), (1, 0), (2, 2), (1, 2)):
+            lib.asfd_debug_fail_allocations(k)
+            try:
+                with pytest.raises(capi.AsfdError) as ei:
+                    plan.execute_host(host_in, host_out)
+            finally:
+                lib.asfd_debug_fail_allocations(-1)
+            assert ei.value.status == capi.ASFD_ERR_NOMEM
+            # the transform's pair stays once allocated; a refused pair leaves nothing
+            assert lib.asfd_debug_live_buffers() == tables + kept
+        plan.execute_host(host_in, host_out)
+        assert lib.asfd_debug_live_buffers() == tables + 4
+        out = plan.execute(u1_t).cpu().numpy()
+    assert lib.asfd_debug_live_buffers() == base
+    for x in (out, host_out.numpy()):
+        assert float(np.linalg.norm(x - ref) / np.linalg.norm(ref)) < 1e-5
