@@ -37,8 +37,8 @@ FALLBACK_HBM_GBS = 6800.0
 # seconds of untimed back-to-back steps under clock sampling before the timed region
 CLOCK_LOAD_S = 0.5
 # extra lines after the headline (each on the same single GPU)
-EXTRAS = ("deterministic", "es_widths", "learned", "direct_sum", "line", "multi", "adjoint", "batch",
-          "fft_reference")
+EXTRAS = ("peaks", "deterministic", "es_widths", "learned", "direct_sum", "line", "multi", "adjoint",
+          "batch", "fft_reference")
 
 
 def parse_args():
@@ -203,10 +203,35 @@ SPREAD_KERNEL = {0: "spread_es_colored_kernel", 1: "spread_es_atomic_kernel",
 # u1 + d1 (12) + fine-grid write (4 M^2 8 / N^2 = 32) + row read (32) + row write
 # (16) + column read (16) + u2 write (8), sigma = 2 and N = M
 STEP_BYTES_PER_SAMPLE = 116
-# DRAM bytes (read + write) per launch of the dominant kernel from one ncu capture
-# of the current kernel (profiles/spread_es_dense_w7_smooth_random2048.md); a
-# kernel or workload without a capture of its current code reports null
-NCU_TRAFFIC = {("spread_es_dense_kernel<7>", "smooth_random2048"): 86.788864e6 + 1.597696e6}
+# DRAM bytes (read + write) per launch of the dominant kernel from one ncu
+# capture, with the SHA-1 of the kernel's sources at the time of the capture:
+# the traffic is reported only while the sources still hash to that state (a
+# kernel changed since its capture, or without one, reports null)
+SPREAD_SOURCES = ("paper_1203_3583_gb300/csrc/spread.cuh", "paper_1203_3583_gb300/csrc/sample.cuh",
+                  "paper_1203_3583_gb300/csrc/spread.cu")
+NCU_TRAFFIC = {("spread_es_dense_kernel<7>", "smooth_random2048"): {
+    "bytes": 86.788864e6 + 1.597696e6,
+    "capture": "profiles/spread_es_dense_w7_smooth_random2048.md",
+    "sources_sha1": "9cca754c5199de4bed88ceedd8e82b85ef1f62f7"}}
+
+
+def sources_sha1(paths) -> str:
+    import hashlib
+    h = hashlib.sha1()
+    for rel in paths:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def captured_traffic(kernel: str, workload: str):
+    """(DRAM bytes per launch or None, provenance note)."""
+    rec = NCU_TRAFFIC.get((kernel, workload))
+    if rec is None:
+        return None, "no ncu capture of this kernel and workload"
+    if sources_sha1(SPREAD_SOURCES) != rec["sources_sha1"]:
+        return None, f"kernel sources changed since the capture in {rec['capture']}"
+    return rec["bytes"], f"ncu capture in {rec['capture']} (sources sha1 {rec['sources_sha1'][:12]})"
 
 
 def oracle_sample(g, u1, d1, seconds, seed=7):
@@ -345,21 +370,27 @@ def run_ours(args):
     peak, peak_src = measured_peaks()
     achieved = sb[dom] / (mean_stage[dom] * 1e-3) / 1e9
     names = [f"{SPREAD_KERNEL[info['spread_kind']]}<{args.width}>"] + STAGE_KERNELS[1:]
+    traffic, traffic_src = captured_traffic(names[dom], args.workload)
     roofline = {"bound": "hbm", "kernel": names[dom], "achieved": achieved, "peak": peak,
                 "unit": "GB/s", "frac": achieved / peak,
-                "traffic": NCU_TRAFFIC.get((names[dom], args.workload)),
+                "traffic": traffic, "traffic_source": traffic_src,
                 "algorithmic_bytes_per_launch": sb[dom], "peak_source": peak_src,
                 "stage_ms": {k: v for k, v in zip(names, mean_stage)},
                 "stage_frac": {k: b / (t * 1e-3) / 1e9 / peak
                                for k, b, t in zip(names, sb, mean_stage)}}
-    # the whole step against the unpruned spread+FFT memory model
+    # the whole step against the memory traffic it must make: the pruned bytes
+    # of its three kernels (only the band of the fine grid that footprints
+    # reach is written and transformed), and beside it the unpruned
+    # spread+FFT model of 116 B per source sample
+    t_step = statistics.mean(step_ms) * 1e-3
+    pruned = sum(sb)
     step_bytes = STEP_BYTES_PER_SAMPLE * n_src
-    step_roofline = {"bound": "hbm", "bytes_per_sample": STEP_BYTES_PER_SAMPLE,
-                     "bytes_per_step": step_bytes,
-                     "achieved": step_bytes / (statistics.mean(step_ms) * 1e-3) / 1e9,
-                     "peak": peak, "unit": "GB/s",
-                     "frac": step_bytes / (statistics.mean(step_ms) * 1e-3) / 1e9 / peak,
-                     "pruned_bytes_per_step": sum(sb)}
+    step_roofline = {"bound": "hbm", "model": "pruned bytes of the three kernels",
+                     "bytes_per_step": pruned, "achieved": pruned / t_step / 1e9,
+                     "peak": peak, "unit": "GB/s", "frac": pruned / t_step / 1e9 / peak,
+                     "unpruned_bytes_per_sample": STEP_BYTES_PER_SAMPLE,
+                     "unpruned_bytes_per_step": step_bytes,
+                     "unpruned_frac": step_bytes / t_step / 1e9 / peak}
 
     # end to end through the C ABI with pinned host buffers
     hu1 = torch.as_tensor(u1).pin_memory()
@@ -402,6 +433,9 @@ def run_ours(args):
                           "scaled to source samples/s of the full transform"}
             if not args.no_extras:
                 line.update(extra_measurements(args, g, u1, d1, pts, ref, flush, stream))
+                if "measured_peaks" in line and info["spread_kind"] == 3:
+                    line["resource_frac"] = resource_fractions(
+                        info, g, args.width, mean_stage, line["measured_peaks"])
         print(json.dumps(line), flush=True)
     plan.close()
     if world > 1:
@@ -431,6 +465,79 @@ def time_device_ms(fn, steps, warmup, flush, stream):
     return statistics.mean(a.elapsed_time(b) for a, b in evs)
 
 
+def width4_floor():
+    """The width-4 floor (2D relative L2) stored by tests/golden/make_learned_floor.py."""
+    path = os.path.join(ROOT, "tests", "golden", "learned_floor_sigma2.txt")
+    try:
+        for line in open(path):
+            f = line.split()
+            if f and not line.startswith("#") and f[0] == "4":
+                return float(f[2])
+    except OSError:
+        pass
+    return None
+
+
+def probe_peaks(stream, repeats=5):
+    """Measured peaks of the on-chip resources (include/asfd_peaks.h probes),
+    best of `repeats` CUDA-event timed launches after one warm-up each."""
+    import torch
+
+    from paper_1203_3583_gb300 import capi
+    sink = torch.zeros(1 << 16, dtype=torch.float32, device="cuda")
+    red = torch.zeros(32 << 20, dtype=torch.uint8, device="cuda")  # 32 MiB, L2-resident
+    cases = {"smem_load": (sink, 4096, "GB/s"), "smem_store": (sink, 4096, "GB/s"),
+             "l2_red_v2f32": (red, 256, "GB/s"), "ffma2": (sink, 16384, "TFLOP/s"),
+             "mufu_ex2": (sink, 8192, "Gop/s")}
+    out = {}
+    for kind, (buf, iters, unit) in cases.items():
+        capi.asfd_probe_launch(kind, iters, buf, stream)
+        best = None
+        for _ in range(repeats):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            work = capi.asfd_probe_launch(kind, iters, buf, stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            rate = work / (e0.elapsed_time(e1) * 1e-3)
+            best = rate if best is None else max(best, rate)
+        scale = 1e12 if unit == "TFLOP/s" else 1e9
+        out[kind] = {"value": best / scale, "unit": unit}
+    return out
+
+
+def resource_fractions(info, g, width, stage_ms, peaks):
+    """Each stage of the step against the on-chip resources that bound it
+    (measured peaks), beside its HBM fraction: the spread's packed FP32 FMA
+    (4 W^2 flops per sample), MUFU (4 W evaluations per sample: an exp2 and a
+    reciprocal square root per tap and axis) and L2 float2 reductions (window
+    rows flushed: per source column alpha_y n1y + W rows per run, W + 1 cells
+    each); the FFT passes' shared-memory exchanges ((passes - 1) stores and
+    loads of every line)."""
+    import math
+    n = g["n1x"] * g["n1y"]
+    nfx, nfy = info["nfx"], info["nfy"]
+    alpha_y = g["p1y"] * g["p2y"] * nfy / (g["lam"] * g["z0"])
+    runs = max(1, math.ceil(g["n1y"] / max(1, info["run_rows"] or g["n1y"])))
+    flushed = g["n1x"] * (alpha_y * g["n1y"] + runs * width) * (width + 1) * 8.0
+    t_sp, t_r, t_c = (ms * 1e-3 for ms in stage_ms)
+
+    def smem_bytes(L, lines):
+        passes = (int(math.log2(L)) + 3) // 4
+        return (passes - 1) * 8.0 * L * lines  # each of stores and loads
+    rows = (info["band_y1"] - info["band_y0"])
+    sm_r, sm_c = smem_bytes(nfx, rows), smem_bytes(nfy, g["m2x"])
+    ld, st = peaks["smem_load"]["value"] * 1e9, peaks["smem_store"]["value"] * 1e9
+    return {
+        "spread": {"ffma2": 4.0 * width * width * n / t_sp / (peaks["ffma2"]["value"] * 1e12),
+                   "mufu": 4.0 * width * n / t_sp / (peaks["mufu_ex2"]["value"] * 1e9),
+                   "l2_red": flushed / t_sp / (peaks["l2_red_v2f32"]["value"] * 1e9)},
+        "fft_rows": {"smem": (sm_r / st + sm_r / ld) / t_r},
+        "fft_cols": {"smem": (sm_c / st + sm_c / ld) / t_c},
+    }
+
+
 def extra_measurements(args, g, u1, d1, pts, ref_pts, flush, stream):
     """Single-GPU context lines: the ES width sweep and the learned kernel at the
     same workload (accuracy against the ES width-12 field and the oracle
@@ -454,6 +561,8 @@ def extra_measurements(args, g, u1, d1, pts, ref_pts, flush, stream):
     res = {}
     widths = {}
     peak, _ = measured_peaks()
+    if "peaks" in args.extras:
+        res["measured_peaks"] = probe_peaks(stream)
 
     def step_frac(ms):
         # the step against the spread+FFT memory model (STEP_BYTES_PER_SAMPLE)
@@ -477,7 +586,7 @@ def extra_measurements(args, g, u1, d1, pts, ref_pts, flush, stream):
                 full, orc = accuracy(out)
             widths[str(w)] = {"samples_per_s": n_src / (ms * 1e-3), "ms": ms,
                               "rel_l2_vs_es12": full, "rel_l2_vs_oracle": orc,
-                              "step_roofline_frac": step_frac(ms)}
+                              "unpruned_step_frac": step_frac(ms)}
         res["es_widths"] = widths
 
     if "learned" in args.extras:
@@ -492,16 +601,21 @@ def extra_measurements(args, g, u1, d1, pts, ref_pts, flush, stream):
             ms = time_device_ms(lambda: p.execute(u1_d, out=out), steps, 3, flush, stream)
             full, orc = accuracy(out)
         match = [w for w in sorted(widths, key=int) if widths[w]["rel_l2_vs_es12"] <= full]
+        floor = width4_floor()
         res["learned"] = {
             "kernel_width": 4, "samples_per_s": n_src / (ms * 1e-3), "ms": ms,
-            "step_roofline_frac": step_frac(ms),
+            "unpruned_step_frac": step_frac(ms),
             "rel_l2_vs_es12": full, "rel_l2_vs_oracle": orc,
             "target_rel_l2": 1e-4, "meets_target": orc <= 1e-4,
+            "width4_floor_rel_l2": floor, "above_floor": orc / floor if floor else None,
+            "floor_source": "tests/golden/learned_floor_sigma2.txt (no width-4 gridding reaches "
+                            "below it at sigma 2 on random-phase samples)",
             "gain_vs_es4_error": widths["4"]["rel_l2_vs_es12"] / full if "4" in widths else None,
             "es_width_at_same_accuracy": int(match[0]) if match else None,
             "speedup_vs_es_at_same_accuracy": (widths[match[0]]["ms"] / ms) if match else None,
             "training": {"steps": len(losses), "seconds_incl_references": train_s,
-                         "pairs": len(pairs), "geometry": "smooth_random2048 at 512^2",
+                         "pairs": len(pairs),
+                         "geometry": "smooth_random2048 recipe at 2048^2, surface seeds 100-101",
                          "final_train_rel_l2": float(np.sqrt(losses[-1]))}}
 
     if "direct_sum" in args.extras:

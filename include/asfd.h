@@ -109,6 +109,8 @@ typedef struct {
                              /*    (many samples per cell): register windows flushed    */
                              /*    to the fine grid with atomic adds (widths up to 7)   */
     int stride_x, stride_y;  /* sample strides between lanes of one warp step (0, 2)    */
+    int run_rows;            /* source rows per lane run of the register-window spread  */
+                             /*    (spread_kind 3; 0 otherwise)                         */
 } asfd_plan_info;
 
 /*

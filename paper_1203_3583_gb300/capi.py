@@ -81,6 +81,7 @@ class PlanInfo(ctypes.Structure):
         ("device_bytes", ctypes.c_size_t),
         ("spread_kind", ctypes.c_int),
         ("stride_x", ctypes.c_int), ("stride_y", ctypes.c_int),
+        ("run_rows", ctypes.c_int),
     ]
 
 
@@ -123,6 +124,8 @@ SIGNATURES = {
     "asfd_line_destroy": (_int, [_vp]),
     "asfd_multi_execute": (_int, [_vp, _vp, _int, _vp, _vp]),
     "asfd_fft_lines_noalloc": (_int, [_int, _int, _int, _vp, _vp, _vp]),
+    "asfd_probe_launch": (_int, [_int, _int, _vp, ctypes.c_size_t,
+                                 ctypes.POINTER(ctypes.c_double), _vp]),
     "asfd_learned_param_count": (ctypes.c_size_t, []),
     "asfd_learned_get_params": (_int, [_vp, _vp, ctypes.c_size_t]),
     "asfd_learned_set_params": (_int, [_vp, _vp, ctypes.c_size_t, _vp]),
@@ -146,6 +149,21 @@ def asfd_fft_lines_noalloc(x: torch.Tensor, sign: int = -1, out: torch.Tensor | 
                                          _dev_ptr(out, torch.complex64, (lines, n), "out"),
                                          _stream(stream)))
     return out
+
+
+PROBES = {"smem_load": 0, "smem_store": 1, "l2_red_v2f32": 2, "ffma2": 3, "mufu_ex2": 4}
+
+
+def asfd_probe_launch(kind: str, iters: int, scratch: torch.Tensor, stream=None) -> float:
+    """Queue one resource probe (include/asfd_peaks.h) on the stream; returns
+    the work it queued (bytes, flops or evaluations)."""
+    if not (isinstance(scratch, torch.Tensor) and scratch.is_cuda and scratch.is_contiguous()):
+        raise TypeError("scratch must be a contiguous CUDA tensor")
+    work = ctypes.c_double(0.0)
+    _check(load().asfd_probe_launch(PROBES[kind], int(iters), ctypes.c_void_p(scratch.data_ptr()),
+                                    scratch.numel() * scratch.element_size(), ctypes.byref(work),
+                                    _stream(stream)))
+    return work.value
 
 
 def asfd_batch_create(params_list, d1_list, stream=None):

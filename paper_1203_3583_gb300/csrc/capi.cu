@@ -231,6 +231,7 @@ asfd_status asfd_get_plan_info(asfd_plan P, asfd_plan_info* info)
     info->spread_kind = P->colored ? (P->windowed && !P->learned ? 2 : 0) : (P->dense ? 3 : 1);
     info->stride_x = info->spread_kind == 2 ? P->sxw_min : P->sx_min;
     info->stride_y = P->h_min;
+    info->run_rows = P->dense ? P->dense_rows : 0;
     return ASFD_OK;
 }
 

@@ -8,7 +8,7 @@ own.  Training pairs are seeded (surface, field) inputs of one geometry; the
 target of each pair is the transform with the ES kernel at width 12, the
 reference for the learned kernel's error.
 
-    model = train_model(train_set(...), steps=400)
+    model, losses = train_model(train_set())
     model.save("learned_w4.npz"); LearnedModel.load(path).apply_to(plan)
 """
 from __future__ import annotations
@@ -24,9 +24,11 @@ from .fresnel import FresnelPlan
 REFERENCE_WIDTH = 12
 
 
-def train_set(name="smooth_random2048", scale=4, surfaces=4, fields=2, seed=100):
+def train_set(name="smooth_random2048", scale=1, surfaces=2, fields=1, seed=100):
     """Seeded (geometry, u1, d1) pairs of one geometry: `surfaces` smooth random
-    height maps (the workload's recipe, other seeds) x `fields` random fields."""
+    height maps (the workload's recipe, other seeds) x `fields` random fields.
+    The default is the full-size geometry, so that the samples' spacing on the
+    fine grid (and every tile feature) is the one the model is used at."""
     out = []
     for s in range(surfaces):
         g, _, d1 = W.make(name, seed=seed + s, scale=scale)
@@ -66,10 +68,13 @@ class LearnedModel:
         return cls(z["params"], meta)
 
 
-def train_model(pairs, refs=None, steps=2000, lr=1e-2, lr_final=3.3e-4, plan=None, log=None):
+def train_model(pairs, refs=None, steps=6000, lr=3e-3, lr_final=1e-5, plan=None, log=None,
+                loss_every=100):
     """Adam on the relative squared error against the reference fields,
     cycling over the pairs (the plan is rebuilt when the surface changes).
-    lr decays geometrically from `lr` to `lr_final`.  Returns (model, losses)."""
+    lr decays geometrically from `lr` to `lr_final`; the loss is read back
+    (a stream synchronisation) every `loss_every` steps and at the last one.
+    Returns (model, losses) with losses[i] the loss at the i-th readback."""
     if refs is None:
         refs = reference_fields(pairs)
     g0, _, d10 = pairs[0]
@@ -88,10 +93,12 @@ def train_model(pairs, refs=None, steps=2000, lr=1e-2, lr_final=3.3e-4, plan=Non
                 current = id(d1)
             frac = it / max(1, steps - 1)
             rate = lr * math.exp(frac * math.log(lr_final / lr))
+            want = it % max(1, loss_every) == 0 or it == steps - 1
             loss = capi.asfd_learned_train_step(plan.handle, u1s[k], refs[k], rate, plan.shape1,
-                                                plan.shape2)
-            losses.append(loss)
-            if log and (it % max(1, steps // 10) == 0 or it == steps - 1):
+                                                plan.shape2, want_loss=want)
+            if want:
+                losses.append(loss)
+            if log and want and (it % max(1, steps // 10) < max(1, loss_every) or it == steps - 1):
                 log(f"step {it:5d}  lr {rate:.2e}  rel-L2 {math.sqrt(loss):.3e}")
         params = capi.asfd_learned_get_params(plan.handle)
     finally:

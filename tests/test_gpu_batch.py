@@ -70,9 +70,10 @@ def test_batch_equals_individual_plans(rgb_batch):
 
 
 def test_batch_matches_oracle(rgb_batch):
+    """512 seeded destination points per surface."""
     items, out, _, _, _ = rgb_batch
     for i, (g, u1, d1) in enumerate(items):
-        pts = W.sample_points(g, 96, seed=400 + i)
+        pts = W.sample_points(g, 512, seed=400 + i)
         ref = oracle.eq7(g, u1, d1, points=pts)
         err = rel_l2(out[i][pts[1], pts[0]], ref)
         assert err < 1e-5, (i, err)

@@ -6,12 +6,15 @@
 * training gradients: asfd_learned_gradient (forward, loss, adjoint FFT
   passes, table / MLP / deconvolution gradient kernels) equals central finite
   differences of the CPU reference's loss, parameter by parameter;
-* gain: a model trained by the library's own kernels beats the ES kernel at
-  the same width 4 on held-out surfaces, checked against the oracle.
+* accuracy: a model trained by the library's own kernels on held-out
+  surfaces reaches the width-4 floor (the best any width-4 gridding can do,
+  oracle/learned_floor.py) on the 2048^2 workload against the oracle, about
+  4x below the ES kernel of the same width.
 """
 from __future__ import annotations
 
 import math
+import os
 
 import numpy as np
 import pytest
@@ -22,8 +25,11 @@ import oracle  # noqa: E402
 from oracle import learned_ref as R  # noqa: E402
 from paper_1203_3583_gb300 import capi, learned as L, workloads as W  # noqa: E402
 from paper_1203_3583_gb300.fresnel import FresnelPlan  # noqa: E402
+from tests.oracle_cache import sampled  # noqa: E402
 
 pytestmark = pytest.mark.gpu
+
+GOLDEN_FLOOR = os.path.join(os.path.dirname(__file__), "golden", "learned_floor_sigma2.txt")
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -105,18 +111,38 @@ def test_learned_gradient_matches_cpu_finite_differences():
         assert np.any(grad[sl] != 0.0)
 
 
-def test_trained_model_beats_es_at_width_4():
-    pairs = L.train_set(surfaces=4, fields=2, seed=300)
+def _width4_floor():
+    """The smallest relative L2 error any width-4 gridding reaches at sigma = 2
+    on random-phase samples (2D), as written by tests/golden/make_learned_floor.py
+    from the oracle (pinned in tests/test_learned_floor_cpu.py)."""
+    for line in open(GOLDEN_FLOOR):
+        if line.strip() and not line.startswith("#") and line.split()[0] == "4":
+            return float(line.split()[2])
+    raise AssertionError("no width-4 row in " + GOLDEN_FLOOR)
+
+
+def test_learned_reaches_width4_floor_on_smooth_random2048():
+    """The model trained by the library's own kernels (Adam on the GPU, two
+    held-out surfaces of the 2048^2 recipe) against the FP64 oracle of Eq. 7
+    on 4096 seeded points of the 2048^2 workload itself.
+
+    The target of 1e-4 at width 4 lies below the width-4 floor (2.71e-4: no
+    tap table and no per-mode correction of width 4 does better on
+    random-phase samples at sigma = 2), so the bar here is the floor: within
+    15 % above it, never meaningfully below it, and at least 3x better than
+    the ES kernel of the same width on the same points."""
+    floor = _width4_floor()
+    pairs = L.train_set(seed=300)
     model, losses = L.train_model(pairs)
-    assert math.sqrt(losses[-1]) < math.sqrt(losses[0])
-    g, u1, d1 = L.train_set(surfaces=1, fields=1, seed=700)[0]
-    pts = W.sample_points(g, 512, seed=701)
-    ref = oracle.eq7(g, u1, d1, points=pts)
+    assert math.sqrt(losses[-1]) < 0.4 * math.sqrt(losses[0])
+    g, u1, d1, pts, ref = sampled("smooth_random2048", 4096, 103)
+    u1_t = torch.as_tensor(u1, device="cuda")
     with FresnelPlan(g, d1, kind="learned") as p:
         model.apply_to(p)
-        lw = p.execute(torch.as_tensor(u1, device="cuda")).cpu().numpy()[pts[1], pts[0]]
+        lw = p.execute(u1_t).cpu().numpy()[pts[1], pts[0]]
     with FresnelPlan(g, d1, kernel_width=4) as p:
-        es4 = p.execute(torch.as_tensor(u1, device="cuda")).cpu().numpy()[pts[1], pts[0]]
+        es4 = p.execute(u1_t).cpu().numpy()[pts[1], pts[0]]
     e_learned = np.linalg.norm(lw - ref) / np.linalg.norm(ref)
     e_es4 = np.linalg.norm(es4 - ref) / np.linalg.norm(ref)
-    assert e_learned < 0.7 * e_es4, (e_learned, e_es4)
+    assert 0.9 * floor < e_learned < 1.15 * floor, (e_learned, floor)
+    assert e_learned < e_es4 / 3.0, (e_learned, e_es4)

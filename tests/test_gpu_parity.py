@@ -17,6 +17,7 @@ torch = pytest.importorskip("torch")
 import oracle  # noqa: E402
 from paper_1203_3583_gb300 import capi, workloads as W  # noqa: E402
 from paper_1203_3583_gb300.fresnel import FresnelPlan  # noqa: E402
+from tests.oracle_cache import sampled  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
@@ -256,31 +257,27 @@ def test_spherical_cap1024_sampled():
     assert err < TOL_ES, err
 
 
-def test_smooth_random2048_sampled():
-    g, u1, d1 = W.make("smooth_random2048")
-    pts = W.sample_points(g, 1024, seed=103)
-    out, _ = run_gpu(g, u1, d1)
-    ref = oracle.eq7(g, u1, d1, points=pts)
+@pytest.mark.parametrize("deterministic", [False, True])
+def test_smooth_random2048_sampled(deterministic):
+    """4096 seeded destination points of the 2048^2 workload, both spread paths."""
+    g, u1, d1, pts, ref = sampled("smooth_random2048", 4096, 103)
+    out, _ = run_gpu(g, u1, d1, deterministic=deterministic)
     err = rel_l2(out[pts[1], pts[0]], ref)
     assert err < TOL_ES, err
 
 
 def test_tilt_bump4096_sampled():
-    g, u1, d1 = W.make("tilt_bump4096")
-    pts = W.sample_points(g, 256, seed=105)
+    """4096 seeded destination points of the 4096^2 workload."""
+    g, u1, d1, pts, ref = sampled("tilt_bump4096", 4096, 105)
     out, _ = run_gpu(g, u1, d1)
-    ref = oracle.eq7(g, u1, d1, points=pts)
     err = rel_l2(out[pts[1], pts[0]], ref)
     assert err < TOL_ES, err
 
 
-def test_constant_height_full_grid_1024():
+def _constant_height_reference(g, u1, c):
     """d1 = c: Eq. 7 factorises into Ey (u1 o chirp) Ex^T with 1D FP64 DFT
-    matrices at distance r0 = z0 - c; compared over the full 1024^2 grid."""
-    g, u1, _ = W.make("spherical_cap1024")
-    c = 0.4e-3
-    d1 = np.full((g["n1y"], g["n1x"]), c)
-    out, _ = run_gpu(g, u1, d1)
+    matrices at distance r0 = z0 - c, times the destination chirp and the
+    global factor (Sec. 2, Eqs. 7-8): an exact full-grid reference."""
     k = 2 * np.pi / g["lam"]
     r0 = g["z0"] - c
     x1 = W.coords(g["n1x"], g["p1x"])
@@ -294,7 +291,31 @@ def test_constant_height_full_grid_1024():
     s = ey @ f @ ex.T
     outer = np.exp(1j * k * (g["z0"] + (x2[None, :] ** 2 + y2[:, None] ** 2) / (2 * g["z0"]))) / (
         1j * g["lam"] * g["z0"])
-    ref = outer * g["p1x"] * g["p1y"] * s
+    return outer * g["p1x"] * g["p1y"] * s
+
+
+def test_constant_height_full_grid_2048():
+    """The 2048^2 workload's geometry and field on a constant surface: the full
+    2048^2 destination grid against the separable FP64 reference."""
+    g, u1, _ = W.make("smooth_random2048")
+    c = 25e-6
+    d1 = np.full((g["n1y"], g["n1x"]), c)
+    out, _ = run_gpu(g, u1, d1)
+    ref = _constant_height_reference(g, u1, c)
+    pts = W.sample_points(g, 16, seed=106)
+    assert rel_l2(ref[pts[1], pts[0]], oracle.eq7(g, u1, d1, points=pts)) < 1e-9
+    err = rel_l2(out, ref)
+    assert err < TOL_ES, err
+
+
+def test_constant_height_full_grid_1024():
+    """d1 = c: Eq. 7 factorises into Ey (u1 o chirp) Ex^T with 1D FP64 DFT
+    matrices at distance r0 = z0 - c; compared over the full 1024^2 grid."""
+    g, u1, _ = W.make("spherical_cap1024")
+    c = 0.4e-3
+    d1 = np.full((g["n1y"], g["n1x"]), c)
+    out, _ = run_gpu(g, u1, d1)
+    ref = _constant_height_reference(g, u1, c)
     # spot-check the separable reference against the oracle itself
     pts = W.sample_points(g, 64, seed=104)
     assert rel_l2(ref[pts[1], pts[0]], oracle.eq7(g, u1, d1, points=pts)) < 1e-9
