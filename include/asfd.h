@@ -182,10 +182,13 @@ asfd_status asfd_set_workspace(asfd_plan plan, void* ws_dev, size_t bytes);
 asfd_status asfd_execute(asfd_plan plan, const float* u1_dev, float* u2_dev, void* stream);
 
 /*
- * Same transform on HOST buffers: copies u1 host->device, runs asfd_execute,
- * copies u2 device->host, and synchronises `stream` before returning.
- * u1_host: [n1y][n1x] complex; u2_host: [m2y][m2x] complex.  The device
- * copies of u1 and u2 are work buffers of the plan (see asfd_set_workspace).
+ * Same transform on HOST buffers, synchronising `stream` before returning.
+ * u1_host: [n1y][n1x] complex; u2_host: [m2y][m2x] complex.  Page-locked
+ * buffers (cudaHostAlloc, cudaMallocHost, cudaHostRegister, PyTorch's
+ * pin_memory) are read by the spread and written by the column pass in
+ * place, over the host link, while those kernels compute; other host memory
+ * is copied to and from device copies that are work buffers of the plan
+ * (see asfd_set_workspace).
  * Errors: ASFD_ERR_ARG, ASFD_ERR_NOMEM (work buffers), ASFD_ERR_CUDA.
  */
 asfd_status asfd_execute_host(asfd_plan plan, const float* u1_host, float* u2_host, void* stream);

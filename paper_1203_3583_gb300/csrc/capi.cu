@@ -53,6 +53,19 @@ asfd_status on_device(int dev, F&& fn)
     return s;
 }
 
+// Device address through which kernels on the current device read and write
+// the page-locked host memory at p (cudaHostAlloc, cudaMallocHost,
+// cudaHostRegister), or NULL for any other memory.
+void* mapped_host_address(const void* p)
+{
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+}
+
 }  // namespace
 }  // namespace asfd
 
@@ -191,20 +204,27 @@ asfd_status asfd_execute_host(asfd_plan P, const float* u1_host, float* u2_host,
     if (!P || !u1_host || !u2_host) return fail(ASFD_ERR_ARG, "plan, u1 or u2 is NULL");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     return on_device(P->device, [&]() -> asfd_status {
-        // staging buffers: work buffers of the plan (its own, allocated on
-        // first use, or carved from the caller's workspace)
+        // Page-locked host memory is read by the spread and written by the
+        // column pass in place, over the host link, while they compute; any
+        // other host memory goes through the plan's staging buffers (work
+        // buffers: its own, allocated on first use, or the caller's workspace).
+        const float2* in = static_cast<const float2*>(mapped_host_address(u1_host));
+        float2* out = static_cast<float2*>(mapped_host_address(u2_host));
         const size_t b1 = sizeof(float2) * (size_t)P->prm.n1x * P->prm.n1y;
         const size_t b2 = sizeof(float2) * (size_t)P->prm.m2x * P->prm.m2y;
-        asfd_status s = plan_ensure_work(P, kWorkTransform | kWorkStaging);
+        asfd_status s = plan_ensure_work(P, kWorkTransform | (in && out ? 0u : kWorkStaging));
         if (s != ASFD_OK) return s;
-        ASFD_CUDA(cudaMemcpyAsync(P->stage_u1, u1_host, b1, cudaMemcpyHostToDevice, st));
-        s = launch_spread(P, P->stage_u1, st);
+        if (!in) {
+            ASFD_CUDA(cudaMemcpyAsync(P->stage_u1, u1_host, b1, cudaMemcpyHostToDevice, st));
+            in = P->stage_u1;
+        }
+        s = launch_spread(P, in, st);
         if (s != ASFD_OK) return s;
         s = launch_fft_rows(P, st);
         if (s != ASFD_OK) return s;
-        s = launch_fft_cols(P, P->stage_u2, st);
+        s = launch_fft_cols(P, out ? out : P->stage_u2, st);
         if (s != ASFD_OK) return s;
-        ASFD_CUDA(cudaMemcpyAsync(u2_host, P->stage_u2, b2, cudaMemcpyDeviceToHost, st));
+        if (!out) ASFD_CUDA(cudaMemcpyAsync(u2_host, P->stage_u2, b2, cudaMemcpyDeviceToHost, st));
         ASFD_CUDA(cudaStreamSynchronize(st));
         return ASFD_OK;
     });

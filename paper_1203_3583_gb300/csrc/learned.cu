@@ -174,19 +174,34 @@ __global__ void residual_kernel(const float2* __restrict__ u2, const float2* __r
     g[i] = make_float2(sc * (a.x - b.x), sc * (a.y - b.y));
 }
 
-// dL/dcorr_x[mx] = Re sum_my conj(g) u2 / corr_x[mx] (one thread per column)
-__global__ void deconv_grad_x_kernel(const float2* __restrict__ g, const float2* __restrict__ u2,
-                                     const float* __restrict__ corr, int m2x, int m2y,
-                                     float* __restrict__ out)
+// dL/dcorr_x[mx] = Re sum_my conj(g) u2 / corr_x[mx]: blocks of 32 columns x
+// 8 thread rows over a slab of destination rows; the slab's column sums are
+// added atomically to out (zeroed by the caller)
+constexpr int kDeconvSlabs = 64;
+
+__global__ void __launch_bounds__(256) deconv_grad_x_kernel(const float2* __restrict__ g,
+                                                            const float2* __restrict__ u2,
+                                                            const float* __restrict__ corr,
+                                                            int m2x, int m2y, float* __restrict__ out)
 {
-    const int mx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (mx >= m2x) return;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int mx = blockIdx.x * 32 + tx;
+    const int slab = (m2y + gridDim.y - 1) / gridDim.y;
+    const int y0 = blockIdx.y * slab, y1 = min(m2y, y0 + slab);
     float s = 0.f;
-    for (int my = 0; my < m2y; ++my) {
-        const float2 a = g[(size_t)my * m2x + mx], b = u2[(size_t)my * m2x + mx];
-        s += a.x * b.x + a.y * b.y;
+    if (mx < m2x)
+        for (int my = y0 + ty; my < y1; my += 8) {
+            const float2 a = g[(size_t)my * m2x + mx], b = u2[(size_t)my * m2x + mx];
+            s += a.x * b.x + a.y * b.y;
+        }
+    __shared__ float red[8][33];
+    red[ty][tx] = s;
+    __syncthreads();
+    if (ty == 0 && mx < m2x) {
+        float t = 0.f;
+        for (int r = 0; r < 8; ++r) t += red[r][tx];
+        atomicAdd(&out[mx], t / corr[mx]);
     }
-    out[mx] = s / corr[mx];
 }
 
 // dL/dcorr_y[my] (one block per row)
@@ -296,23 +311,35 @@ __global__ void __launch_bounds__(256) table_grad_kernel(TGArgs a)
             }
         }
     }
-    // block reduction of the 2 W K sums
-    __shared__ float red[8][kLearnTableSize];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x / 32;
+    // block reduction of the 2 W K = 64 sums: within each warp a
+    // reduce-scatter by recursive halving (at offset o a lane keeps the half
+    // of its values selected by lane bit o and adds its partner's copy of
+    // that half), after which lane l holds the warp's sums of entries 2l and
+    // 2l + 1; then the 8 warps' sums are added in shared memory
+    static_assert(2 * W * K == 64, "reduce-scatter of 64 values over 32 lanes");
+    float v[64];
 #pragma unroll
     for (int i = 0; i < W; ++i)
 #pragma unroll
         for (int k = 0; k < K; ++k) {
-            float vx = gx[i][k], vy = gy[i][k];
-            for (int o = 16; o > 0; o >>= 1) {
-                vx += __shfl_xor_sync(0xffffffffu, vx, o);
-                vy += __shfl_xor_sync(0xffffffffu, vy, o);
-            }
-            if (lane == 0) {
-                red[wid][i * K + k] = vx;
-                red[wid][(W + i) * K + k] = vy;
-            }
+            v[i * K + k] = gx[i][k];
+            v[(W + i) * K + k] = gy[i][k];
         }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x / 32;
+#pragma unroll
+    for (int lvl = 0; lvl < 5; ++lvl) {
+        const int o = 16 >> lvl, half = 32 >> lvl;
+        const bool upper = (lane & o) != 0;
+#pragma unroll
+        for (int i = 0; i < half; ++i) {
+            const float send = upper ? v[i] : v[i + half];
+            const float keep = upper ? v[i + half] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
+    }
+    __shared__ float red[8][kLearnTableSize];
+    red[wid][2 * lane] = v[0];
+    red[wid][2 * lane + 1] = v[1];
     __syncthreads();
     if (threadIdx.x < kLearnTableSize) {
         float s = 0.f;
@@ -526,8 +553,9 @@ asfd_status learned_gradient(asfd_plan_s* P, const float2* u1, const float2* ref
     residual_kernel<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(P->lu2, ref, m, P->lred, P->lres);
     ASFD_CUDA(cudaMemsetAsync(P->lgrad, 0, sizeof(float) * kLearnParams, st));
     // deconvolution correction gradients
-    deconv_grad_x_kernel<<<(m2x + 127) / 128, 128, 0, st>>>(P->lres, P->lu2, P->lcorr, m2x, m2y,
-                                                            P->lcgrad);
+    ASFD_CUDA(cudaMemsetAsync(P->lcgrad, 0, sizeof(float) * m2x, st));
+    deconv_grad_x_kernel<<<dim3((m2x + 31) / 32, kDeconvSlabs), 256, 0, st>>>(
+        P->lres, P->lu2, P->lcorr, m2x, m2y, P->lcgrad);
     deconv_grad_y_kernel<<<m2y, 256, 0, st>>>(P->lres, P->lu2, P->lcorr + m2x, m2x, P->lcgrad + m2x);
     cheb_grad_kernel<<<1, 256, 0, st>>>(P->lcgrad, m2x, P->lgrad + kLpDx);
     cheb_grad_kernel<<<1, 256, 0, st>>>(P->lcgrad + m2x, m2y, P->lgrad + kLpDy);

@@ -68,7 +68,7 @@ class LearnedModel:
         return cls(z["params"], meta)
 
 
-def train_model(pairs, refs=None, steps=6000, lr=3e-3, lr_final=1e-5, plan=None, log=None,
+def train_model(pairs, refs=None, steps=10000, lr=3e-3, lr_final=1e-5, plan=None, log=None,
                 loss_every=100):
     """Adam on the relative squared error against the reference fields,
     cycling over the pairs (the plan is rebuilt when the surface changes).

@@ -49,8 +49,8 @@ def test_workspace_plan_allocates_nothing_and_matches_oracle(lib, deterministic)
         try:
             u1_t = torch.as_tensor(u1, device="cuda")
             out = plan.execute(u1_t)
-            host = torch.empty(plan.shape2, dtype=torch.complex64).pin_memory()
-            plan.execute_host(torch.as_tensor(u1).pin_memory(), host)
+            host = torch.empty(plan.shape2, dtype=torch.complex64)  # pageable: staged
+            plan.execute_host(torch.as_tensor(u1).clone(), host)
             gu2 = torch.as_tensor(np.conj(np.asarray(out.cpu())), device="cuda")
             gu1 = torch.empty_like(u1_t)
             gd1 = torch.empty(plan.shape1, dtype=torch.float32, device="cuda")
@@ -80,8 +80,8 @@ def test_workspace_replaces_own_buffers_and_detaches(lib):
         a = plan.execute(u1_t).cpu().numpy()
         # the first execution allocated the fine grid and the row buffer
         assert lib.asfd_debug_live_buffers() - base == tables + 2
-        host = torch.empty(plan.shape2, dtype=torch.complex64).pin_memory()
-        plan.execute_host(torch.as_tensor(u1).pin_memory(), host)
+        host = torch.empty(plan.shape2, dtype=torch.complex64)  # pageable: staged
+        plan.execute_host(torch.as_tensor(u1).clone(), host)
         assert lib.asfd_debug_live_buffers() - base == tables + 4
         plan.set_workspace(torch.empty(capi.asfd_workspace_bytes(plan.params), dtype=torch.uint8,
                                        device="cuda"))
