@@ -183,12 +183,13 @@ asfd_status asfd_execute(asfd_plan plan, const float* u1_dev, float* u2_dev, voi
 
 /*
  * Same transform on HOST buffers, synchronising `stream` before returning.
- * u1_host: [n1y][n1x] complex; u2_host: [m2y][m2x] complex.  Page-locked
- * buffers (cudaHostAlloc, cudaMallocHost, cudaHostRegister, PyTorch's
- * pin_memory) are read by the spread and written by the column pass in
- * place, over the host link, while those kernels compute; other host memory
- * is copied to and from device copies that are work buffers of the plan
- * (see asfd_set_workspace).
+ * u1_host: [n1y][n1x] complex; u2_host: [m2y][m2x] complex.  A page-locked
+ * u1 (cudaHostAlloc, cudaMallocHost, cudaHostRegister, PyTorch's
+ * pin_memory) is read by the spread in place, over the host link, while it
+ * computes; a pageable u1 is copied to a device copy first.  u2 is formed in
+ * a device copy and, when page-locked, copied to the host in column blocks
+ * on a stream of the plan while the column pass transforms the next block.
+ * The device copies are work buffers of the plan (see asfd_set_workspace).
  * Errors: ASFD_ERR_ARG, ASFD_ERR_NOMEM (work buffers), ASFD_ERR_CUDA.
  */
 asfd_status asfd_execute_host(asfd_plan plan, const float* u1_host, float* u2_host, void* stream);

@@ -21,6 +21,7 @@ constexpr int kSrcTile = 16;  // source tiles are kSrcTile x kSrcTile samples
 constexpr int kColTileY = 32; // rows of a tile of the conflict-free spreading kernel
 constexpr int kMaxRingWidth = 14;  // widest kernel of the conflict-free spreading path (no spills)
 constexpr int kMaxWindowWidth = 7;  // widest kernel of the register-window spreading path
+constexpr int kHostColBlocks = 4;   // column blocks whose copies to the host overlap the column pass
 
 // Learned spreading kernel: width kLearnW, per-source-tile polynomial of
 // degree kLearnDeg per tap and axis in t = 2 dx - 1, an MLP of kLearnFeat
@@ -148,6 +149,10 @@ struct asfd_plan_s {
     double* lred = nullptr;         // [2] loss reductions
     float2* stage_u1 = nullptr;     // staging for asfd_execute_host (work buffer)
     float2* stage_u2 = nullptr;
+    // asfd_execute_host: a stream for the device-to-host copies of column
+    // blocks and the events that order them after the column pass
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t copy_ev[asfd::kHostColBlocks + 1] = {};
 
     std::vector<asfd::DevBuf> owned;
     size_t device_bytes = 0;
@@ -183,6 +188,9 @@ asfd_status multi_execute(asfd_plan_s* const* plans, const float2* const* u1, in
                           float2* u2, cudaStream_t st);
 asfd_status launch_fft_rows(asfd_plan_s* P, cudaStream_t st);
 asfd_status launch_fft_cols(asfd_plan_s* P, float2* u2, cudaStream_t st);
+// column pass over the kept columns [col0, col1) only
+asfd_status launch_fft_cols_range(asfd_plan_s* P, float2* u2, int col0, int col1,
+                                  cudaStream_t st);
 asfd_status launch_fft_lines(int n, int lines, int sign, const float2* in, float2* out,
                              cudaStream_t st);
 asfd_status launch_fft_cols_adj(asfd_plan_s* P, const float2* g, cudaStream_t st);

@@ -1,5 +1,6 @@
 // The exported C ABI (include/asfd.h): argument checks, plan lifetime, and
 // the forward transform as three kernels on the caller's stream.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -204,15 +205,20 @@ asfd_status asfd_execute_host(asfd_plan P, const float* u1_host, float* u2_host,
     if (!P || !u1_host || !u2_host) return fail(ASFD_ERR_ARG, "plan, u1 or u2 is NULL");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     return on_device(P->device, [&]() -> asfd_status {
-        // Page-locked host memory is read by the spread and written by the
-        // column pass in place, over the host link, while they compute; any
-        // other host memory goes through the plan's staging buffers (work
-        // buffers: its own, allocated on first use, or the caller's workspace).
+        // u1 in page-locked host memory is read by the spread in place, over
+        // the host link, while it computes (as fast as a copy, and hidden
+        // behind the spread); pageable u1 is copied to the plan's staging
+        // buffer first.  u2 is written to the staging buffer by the column
+        // pass, in column blocks, and each block is copied to the host while
+        // the next one is transformed (the link takes these copies faster
+        // than kernel stores to host memory).  Staging buffers are work
+        // buffers (the plan's own, allocated on first use, or the workspace).
         const float2* in = static_cast<const float2*>(mapped_host_address(u1_host));
-        float2* out = static_cast<float2*>(mapped_host_address(u2_host));
+        const bool out_locked = mapped_host_address(u2_host) != nullptr;
+        const int m2x = P->prm.m2x, m2y = P->prm.m2y;
         const size_t b1 = sizeof(float2) * (size_t)P->prm.n1x * P->prm.n1y;
-        const size_t b2 = sizeof(float2) * (size_t)P->prm.m2x * P->prm.m2y;
-        asfd_status s = plan_ensure_work(P, kWorkTransform | (in && out ? 0u : kWorkStaging));
+        const size_t b2 = sizeof(float2) * (size_t)m2x * m2y;
+        asfd_status s = plan_ensure_work(P, kWorkTransform | kWorkStaging);
         if (s != ASFD_OK) return s;
         if (!in) {
             ASFD_CUDA(cudaMemcpyAsync(P->stage_u1, u1_host, b1, cudaMemcpyHostToDevice, st));
@@ -222,9 +228,34 @@ asfd_status asfd_execute_host(asfd_plan P, const float* u1_host, float* u2_host,
         if (s != ASFD_OK) return s;
         s = launch_fft_rows(P, st);
         if (s != ASFD_OK) return s;
-        s = launch_fft_cols(P, out ? out : P->stage_u2, st);
-        if (s != ASFD_OK) return s;
-        if (!out) ASFD_CUDA(cudaMemcpyAsync(u2_host, P->stage_u2, b2, cudaMemcpyDeviceToHost, st));
+        const int nblk = (out_locked && m2x >= 256 * kHostColBlocks) ? kHostColBlocks : 1;
+        if (nblk == 1) {
+            s = launch_fft_cols(P, P->stage_u2, st);
+            if (s != ASFD_OK) return s;
+            ASFD_CUDA(cudaMemcpyAsync(u2_host, P->stage_u2, b2, cudaMemcpyDeviceToHost, st));
+        } else {
+            if (!P->copy_stream) {
+                ASFD_CUDA(cudaStreamCreateWithFlags(&P->copy_stream, cudaStreamNonBlocking));
+                for (cudaEvent_t& e : P->copy_ev)
+                    ASFD_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+            }
+            const size_t pitch = sizeof(float2) * (size_t)m2x;
+            // block boundaries on multiples of 64 columns (whole column-pass blocks)
+            const int step = (m2x / nblk + 63) / 64 * 64;
+            for (int k = 0; k < nblk; ++k) {
+                const int c0 = k * step, c1 = std::min(m2x, c0 + step);
+                if (c0 >= c1) break;
+                s = launch_fft_cols_range(P, P->stage_u2, c0, c1, st);
+                if (s != ASFD_OK) return s;
+                ASFD_CUDA(cudaEventRecord(P->copy_ev[k], st));
+                ASFD_CUDA(cudaStreamWaitEvent(P->copy_stream, P->copy_ev[k], 0));
+                ASFD_CUDA(cudaMemcpy2DAsync(reinterpret_cast<float2*>(u2_host) + c0, pitch,
+                                            P->stage_u2 + c0, pitch, sizeof(float2) * (c1 - c0),
+                                            m2y, cudaMemcpyDeviceToHost, P->copy_stream));
+            }
+            ASFD_CUDA(cudaEventRecord(P->copy_ev[kHostColBlocks], P->copy_stream));
+            ASFD_CUDA(cudaStreamWaitEvent(st, P->copy_ev[kHostColBlocks], 0));
+        }
         ASFD_CUDA(cudaStreamSynchronize(st));
         return ASFD_OK;
     });
@@ -297,6 +328,9 @@ asfd_status asfd_destroy(asfd_plan P)
     cudaGetDevice(&prev);
     cudaSetDevice(P->device);
     cudaDeviceSynchronize();
+    for (cudaEvent_t e : P->copy_ev)
+        if (e) cudaEventDestroy(e);
+    if (P->copy_stream) cudaStreamDestroy(P->copy_stream);
     free_all(P);
     cudaSetDevice(prev);
     delete P;

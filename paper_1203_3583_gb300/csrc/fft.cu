@@ -142,7 +142,8 @@ cudaError_t cols_L(const ColArgs& a, cudaStream_t st)
     static cudaError_t attr = cudaSuccess;
     std::call_once(once, [] { attr = set_smem(fft_cols_kernel<L>, C::SMEM_BYTES); });
     if (attr != cudaSuccess) return attr;
-    const int blocks = (a.m2x + C::LPC - 1) / C::LPC;
+    const int blocks = (a.col1 - a.col0 + C::LPC - 1) / C::LPC;
+    if (blocks <= 0) return cudaSuccess;
     fft_cols_kernel<L><<<blocks, C::THREADS, C::SMEM_BYTES, st>>>(a);
     return cudaGetLastError();
 }
@@ -240,6 +241,8 @@ ColArgs make_col_args(const asfd_plan_s* P, float2* u2)
     a.nrows = (P->band_ty1 - P->band_ty0) * kTileY;
     a.m2x = P->prm.m2x;
     a.m2y = P->prm.m2y;
+    a.col0 = 0;
+    a.col1 = P->prm.m2x;
     a.cx = P->cx;
     a.cy = P->cy;
     a.u2 = u2;
@@ -262,6 +265,20 @@ asfd_status launch_fft_rows(asfd_plan_s* P, cudaStream_t st)
 asfd_status launch_fft_cols(asfd_plan_s* P, float2* u2, cudaStream_t st)
 {
     const ColArgs a = make_col_args(P, u2);
+    cudaError_t e = cudaSuccess;
+#define ASFD_COLS(L) e = cols_L<L>(a, st)
+    ASFD_FFT_SWITCH(P->nfy, ASFD_COLS)
+#undef ASFD_COLS
+    if (e != cudaSuccess) return cuda_fail(e, "fft_cols_kernel launch");
+    return ASFD_OK;
+}
+
+asfd_status launch_fft_cols_range(asfd_plan_s* P, float2* u2, int col0, int col1,
+                                  cudaStream_t st)
+{
+    ColArgs a = make_col_args(P, u2);
+    a.col0 = col0;
+    a.col1 = col1;
     cudaError_t e = cudaSuccess;
 #define ASFD_COLS(L) e = cols_L<L>(a, st)
     ASFD_FFT_SWITCH(P->nfy, ASFD_COLS)

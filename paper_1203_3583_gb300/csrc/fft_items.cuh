@@ -52,6 +52,7 @@ struct ColArgs {
     const float2* rows;  // [nrows][m2x] row-pass output (band rows)
     int row0, nrows;
     int m2x, m2y;
+    int col0, col1;      // kept columns [col0, col1) this pass transforms
     const float2* cx;    // [m2x] deconvolution x chirp
     const float2* cy;    // [m2y] same, times the global factor
     float2* u2;          // [m2y][m2x]
@@ -92,8 +93,8 @@ __device__ __forceinline__ void cols_body(const ColArgs& a, int blk, float2* sm,
 {
     using C = ColShape<L, LPC>;
     const int c = tid % LPC, t = tid / LPC;
-    const int col = blk * LPC + c;
-    const bool active = col < a.m2x;
+    const int col = a.col0 + blk * LPC + c;
+    const bool active = col < a.col1;
     const int colc = active ? col : 0;
     const float2 fx = __ldg(&a.cx[colc]);
     const int half = a.m2y / 2;

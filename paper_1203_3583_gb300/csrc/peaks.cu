@@ -36,9 +36,11 @@ __global__ void __launch_bounds__(kProbeThreads) smem_load_probe(float* out, int
     for (int it = 0; it < iters; ++it) {
 #pragma unroll
         for (int k = 0; k < kProbeUnroll; ++k) {
-            // consecutive lanes read consecutive float4 (conflict-free)
-            const int idx = (threadIdx.x + (it * kProbeUnroll + k) * kProbeThreads) &
-                            (kProbeSmemVec - 1);
+            // consecutive lanes read consecutive float4 (conflict-free); the
+            // pattern moves by a warp's width every iteration, so no load
+            // repeats an address of the previous iteration and none can be
+            // hoisted out of the loop
+            const int idx = (threadIdx.x + k * kProbeThreads + it * 32) & (kProbeSmemVec - 1);
             float x, y, z, w;
             asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
                          : "=f"(x), "=f"(y), "=f"(z), "=f"(w)
@@ -60,8 +62,7 @@ __global__ void __launch_bounds__(kProbeThreads) smem_store_probe(float* out, in
     for (int it = 0; it < iters; ++it) {
 #pragma unroll
         for (int k = 0; k < kProbeUnroll; ++k) {
-            const int idx = (threadIdx.x + (it * kProbeUnroll + k) * kProbeThreads) &
-                            (kProbeSmemVec - 1);
+            const int idx = (threadIdx.x + k * kProbeThreads + it * 32) & (kProbeSmemVec - 1);
             asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(base + 16u * (unsigned)idx),
                          "f"(v), "f"(v), "f"(v), "f"(v)
                          : "memory");
