@@ -206,6 +206,16 @@ __device__ __forceinline__ void window_flush(float2* tile, int row, int cx, unsi
     }
 }
 
+// a + b on FP32 pairs (packed FP32x2)
+__device__ __forceinline__ float2 add2(float2 a, float2 b)
+{
+    unsigned long long r;
+    const unsigned long long aa = *reinterpret_cast<const unsigned long long*>(&a);
+    const unsigned long long bb = *reinterpret_cast<const unsigned long long*>(&b);
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(aa), "l"(bb));
+    return *reinterpret_cast<float2*>(&r);
+}
+
 // ES weights of two taps at once (packed FP32x2 arithmetic; the square root
 // and exponential on the MUFU unit as in es_weight_fast).
 __device__ __forceinline__ float2 es_weight2_fast(float2 z, float neg_c2, float beta_log2e)
@@ -238,9 +248,11 @@ __device__ __forceinline__ void window_add(float2 (&acc)[W][WX], bool fresh, int
     float wy[W], wxe[WX];
     const float by = dy - a.half_w;
     const float bx = dx - a.half_w - (float)offn;
+    const float2 bxy = make_float2(by, bx);
 #pragma unroll
     for (int b = 0; b < W; ++b) {
-        const float2 e = es_weight2_fast(make_float2(by + (float)b, bx + (float)b), neg_c2,
+        // tap b's offsets from the sample in y and x, one packed add
+        const float2 e = es_weight2_fast(add2(bxy, make_float2((float)b, (float)b)), neg_c2,
                                          a.beta_log2e);
         wy[b] = e.x;
         wxe[b] = e.y;
@@ -538,6 +550,12 @@ __global__ void __launch_bounds__(32) spread_es_window_kernel(SpreadArgs a)
 // alpha times per sample.  Lanes need no step synchronisation beyond the
 // warp barrier that publishes each row's table entries.
 constexpr int kDenseAhead = 3;  // rows of u1, q and table entries in flight
+// The dense item's window has no spare column: a lane whose first tap column
+// drifts by one inside its run (the x coordinate moves with q down a
+// column, by a fraction of a cell over a run) flushes its window and starts
+// a fresh one at the new column.  That costs one full flush per drift, and
+// saves a column of taps, FMAs and reductions on every sample.
+constexpr int kDenseSpare = 0;
 constexpr int kDenseRing = 4;   // ring slots (> kDenseAhead, power of two)
 constexpr int kDenseRingBytes = kDenseRing * (32 * (8 + 4) + 32);  // per warp
 
@@ -545,7 +563,7 @@ template <int W, bool TAB = false>
 __device__ __forceinline__ void window_atomic_item(const SpreadArgs& a, int it, int lane,
                                                    char* ring, float4* tsm = nullptr)
 {
-    constexpr int WX = W + kWindowSpare;
+    constexpr int WX = W + kDenseSpare;
     const int ncb = (a.n1x + 31) / 32;
     const int nx = (it % ncb) * 32 + lane;
     const int ny0 = (it / ncb) * a.dense_rows;
@@ -579,8 +597,8 @@ __device__ __forceinline__ void window_atomic_item(const SpreadArgs& a, int it, 
                    lf, yy, f0, f1);
         sample_pos(ex, a.ay[nyl], px, a.py[nyl], __ldg(&a.q[(size_t)nyl * a.n1x + nxc]), a.half_w,
                    ll, yy, f0, f1);
-        X0 = (kWindowSpare > 0) ? min(lf, ll) : lf;
-        maxoff = (kWindowSpare > 0 && lf != ll) ? 1 : 0;
+        X0 = (kDenseSpare > 0) ? min(lf, ll) : lf;
+        maxoff = (kDenseSpare > 0 && lf != ll) ? 1 : 0;
     }
     float2 acc[W][WX];
     int R0 = 0;
