@@ -62,7 +62,8 @@ cudaError_t launch_dense(const SpreadArgs& a, int tiles, cudaStream_t st)
     const size_t height = (size_t)(tiles / a.band_ntx) * kTileY;
     cudaError_t e = cudaMemset2DAsync(a.grid + (size_t)r0 * a.nfx + c0, pitch, 0, width, height, st);
     if (e != cudaSuccess) return e;
-    spread_es_dense_kernel<W, TAB><<<(a.dense_items + 3) / 4, 128, 0, st>>>(a, a.dense_items);
+    spread_es_dense_kernel<W, TAB><<<(a.dense_items + kDenseWarps - 1) / kDenseWarps,
+                                     32 * kDenseWarps, 0, st>>>(a, a.dense_items);
     return cudaGetLastError();
 }
 
@@ -109,8 +110,8 @@ asfd_status resident_warps(const void* kernel, long long* slots)
     int dev = 0, sms = 0, per_sm = 0;
     ASFD_CUDA(cudaGetDevice(&dev));
     ASFD_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    ASFD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 128, 0));
-    *slots = (long long)sms * std::max(per_sm, 1) * 4;
+    ASFD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 32 * kDenseWarps, 0));
+    *slots = (long long)sms * std::max(per_sm, 1) * kDenseWarps;
     return ASFD_OK;
 }
 
@@ -183,10 +184,11 @@ asfd_status launch_spread_into(asfd_plan_s* P, const float2* u1, float2* grid, c
     if (a.dense_items <= 0) return ASFD_OK;
     cudaError_t e = cudaSuccess;
     if (P->learned) {
-        spread_es_dense_kernel<kLearnW, true><<<(a.dense_items + 3) / 4, 128, 0, st>>>(a, a.dense_items);
+        spread_es_dense_kernel<kLearnW, true><<<(a.dense_items + kDenseWarps - 1) / kDenseWarps,
+                                               32 * kDenseWarps, 0, st>>>(a, a.dense_items);
     } else {
         switch (P->w) {
-#define ASFD_SI(W) case W: spread_es_dense_kernel<W, false><<<(a.dense_items + 3) / 4, 128, 0, st>>>(a, a.dense_items); break;
+#define ASFD_SI(W) case W: spread_es_dense_kernel<W, false><<<(a.dense_items + kDenseWarps - 1) / kDenseWarps, 32 * kDenseWarps, 0, st>>>(a, a.dense_items); break;
             ASFD_SI(2) ASFD_SI(3) ASFD_SI(4) ASFD_SI(5) ASFD_SI(6) ASFD_SI(7)
 #undef ASFD_SI
             default: return fail(ASFD_ERR_UNSUPPORTED, "dense spread widths are 2..7");

@@ -717,12 +717,16 @@ __device__ __forceinline__ void window_atomic_item(const SpreadArgs& a, int it, 
     }
 }
 
+// warps (items) per block of the dense spread (blocks of 1 or 2 warps with
+// registers capped for more resident warps spilled and ran slower)
+constexpr int kDenseWarps = 4;
+
 template <int W, bool TAB = false>
-__global__ void __launch_bounds__(128) spread_es_dense_kernel(SpreadArgs a, int items)
+__global__ void __launch_bounds__(32 * kDenseWarps) spread_es_dense_kernel(SpreadArgs a, int items)
 {
-    __shared__ float4 tsm[4][TAB ? 8 * W : 1];
-    __shared__ __align__(16) char ring[4][kDenseRingBytes];
-    const int it = blockIdx.x * 4 + threadIdx.x / 32;
+    __shared__ float4 tsm[kDenseWarps][TAB ? 8 * W : 1];
+    __shared__ __align__(16) char ring[kDenseWarps][kDenseRingBytes];
+    const int it = blockIdx.x * kDenseWarps + threadIdx.x / 32;
     if (it < items)
         window_atomic_item<W, TAB>(a, it, threadIdx.x % 32, ring[threadIdx.x / 32],
                                    tsm[threadIdx.x / 32]);
