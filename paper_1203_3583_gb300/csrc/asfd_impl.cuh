@@ -128,6 +128,9 @@ struct asfd_plan_s {
     float2* rows = nullptr;         // [nfy][m2x] row-FFT output (band rows first)
     char* ws = nullptr;             // caller-owned workspace, or NULL
     size_t ws_bytes = 0;
+    bool band_clean = false;        // the band of the fine grid is known to be zero
+                                    // (left so by the forward row pass, which
+                                    // clears each cell it reads)
     unsigned* status = nullptr;     // device status word
     // learned kernel (kind == ASFD_KERNEL_LEARNED)
     bool learned = false;

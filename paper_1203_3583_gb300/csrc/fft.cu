@@ -230,6 +230,7 @@ RowArgs make_row_args(const asfd_plan_s* P)
     a.out = P->rows;
     a.m2x = P->prm.m2x;
     a.tw = P->twx;
+    a.clear = 0;
     return a;
 }
 
@@ -252,13 +253,16 @@ ColArgs make_col_args(const asfd_plan_s* P, float2* u2)
 
 asfd_status launch_fft_rows(asfd_plan_s* P, cudaStream_t st)
 {
-    const RowArgs a = make_row_args(P);
+    RowArgs a = make_row_args(P);
     if (a.nrows <= 0) return ASFD_OK;
+    // the pass reads every band cell once and leaves the band zero
+    a.clear = 1;
     cudaError_t e = cudaSuccess;
 #define ASFD_ROWS(L) e = rows_L<L>(a, st)
     ASFD_FFT_SWITCH(P->nfx, ASFD_ROWS)
 #undef ASFD_ROWS
     if (e != cudaSuccess) return cuda_fail(e, "fft_rows_kernel launch");
+    P->band_clean = true;
     return ASFD_OK;
 }
 
@@ -296,11 +300,14 @@ asfd_status launch_fft_rows_band(asfd_plan_s* P, int ty0, int ty1, int tx0, int 
     a.col_lo = tx0 * kTileX;
     a.col_hi = tx1 * kTileX;
     if (a.nrows <= 0) return ASFD_OK;
+    a.clear = 1;
     cudaError_t e = cudaSuccess;
 #define ASFD_ROWS(L) e = rows_L<L>(a, st)
     ASFD_FFT_SWITCH(P->nfx, ASFD_ROWS)
 #undef ASFD_ROWS
     if (e != cudaSuccess) return cuda_fail(e, "fft_rows_kernel launch");
+    // the given band contains the plan's own band (a sum over several plans)
+    P->band_clean = true;
     return ASFD_OK;
 }
 
@@ -339,6 +346,7 @@ asfd_status launch_fft_rows_adj(asfd_plan_s* P, cudaStream_t st)
 #define ASFD_RA(L) e = rows_adj_L<L>(P->rows, nrows, P->prm.m2x, P->grid, row0, col_lo, col_hi, P->twx, st)
     ASFD_FFT_SWITCH(P->nfx, ASFD_RA)
 #undef ASFD_RA
+    P->band_clean = false;  // the band now holds the adjoint grid
     if (e != cudaSuccess) return cuda_fail(e, "fft_rows_adj_kernel launch");
     return ASFD_OK;
 }

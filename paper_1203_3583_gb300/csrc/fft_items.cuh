@@ -40,12 +40,14 @@ template <int L>
 using ColCfg = ColShape<L, ColCfgSel<L>::LPC>;
 
 struct RowArgs {
-    const float2* grid;  // [nf rows][L] fine grid
+    float2* grid;        // [nf rows][L] fine grid
     int row0, nrows;     // band rows
     int col_lo, col_hi;  // band columns (others are zero)
     float2* out;         // [nrows][m2x] kept bins, order k + m2x/2
     int m2x;
     const float2* tw;
+    int clear;           // 1: zero each band cell once it is loaded (the next
+                         // accumulating spread then needs no separate clear)
 };
 
 struct ColArgs {
@@ -71,12 +73,17 @@ __device__ __forceinline__ void rows_body(const RowArgs& a, int blk, float2* sm,
     const int line = tid / C::TPL, t = tid % C::TPL;
     const int r = blk * C::LPC + line;
     const bool active = r < a.nrows;
-    const float2* src = a.grid + (size_t)(a.row0 + (active ? r : 0)) * L;
+    float2* src = a.grid + (size_t)(a.row0 + (active ? r : 0)) * L;
     float2* dst = a.out + (size_t)(active ? r : 0) * a.m2x;
     const int half = a.m2x / 2;
     const int col_lo = a.col_lo, col_hi = a.col_hi;
+    const bool clear = a.clear != 0;
     auto ld = [&](int i) -> float2 {
-        return (active && i >= col_lo && i < col_hi) ? __ldg(&src[i]) : make_float2(0.f, 0.f);
+        if (!(active && i >= col_lo && i < col_hi)) return make_float2(0.f, 0.f);
+        // each band cell is read by exactly one thread, once
+        const float2 v = src[i];
+        if (clear) src[i] = make_float2(0.f, 0.f);
+        return v;
     };
     auto st = [&](int i, float2 v) {
         if (!active) return;

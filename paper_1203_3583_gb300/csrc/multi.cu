@@ -52,6 +52,7 @@ asfd_status multi_execute(asfd_plan_s* const* plans, const float2* const* u1, in
     ASFD_CUDA(cudaMemset2DAsync(P0->grid + (size_t)ty0 * kTileY * P0->nfx + (size_t)tx0 * kTileX,
                                 pitch, 0, sizeof(float2) * (size_t)(tx1 - tx0) * kTileX,
                                 (size_t)(ty1 - ty0) * kTileY, st));
+    P0->band_clean = false;
     for (int i = 0; i < count; ++i) {
         const asfd_status s = launch_spread_into(plans[i], u1[i], P0->grid, st);
         if (s != ASFD_OK) return s;

@@ -465,6 +465,7 @@ asfd_status plan_ensure_work(asfd_plan_s* P, unsigned need)
     const asfd_params& p = P->prm;
     asfd_status s;
     if ((need & kWorkTransform) && !P->grid) {
+        P->band_clean = false;  // fresh memory
         if ((s = alloc_n(P, &P->grid, (size_t)P->nfx * P->nfy)) != ASFD_OK) return s;
         if ((s = alloc_n(P, &P->rows, (size_t)P->nfy * p.m2x)) != ASFD_OK) {
             release(P, P->grid);
@@ -518,6 +519,7 @@ asfd_status plan_set_workspace(asfd_plan_s* P, void* ws, size_t bytes)
     }
     P->ws = static_cast<char*>(ws);
     P->ws_bytes = ws ? bytes : 0;
+    P->band_clean = false;
     if (ws) {
         char* base = P->ws;
         P->grid = reinterpret_cast<float2*>(base + L.grid);
@@ -584,6 +586,8 @@ asfd_status plan_build_d1(asfd_plan_s* P, const double* d1, cudaStream_t st)
 {
     const asfd_params& p = P->prm;
     const size_t nsrc = (size_t)p.n1x * p.n1y;
+    // the band may move: its new cells were never cleared
+    P->band_clean = false;
     // 1. validate d1 without touching the plan's tables
     ASFD_CUDA(cudaMemsetAsync(P->status, 0, 2 * sizeof(unsigned), st));
     d1_check_kernel<<<(unsigned)((nsrc + 255) / 256), 256, 0, st>>>(d1, nsrc, p.z0, P->status,

@@ -52,26 +52,31 @@ __global__ void __launch_bounds__(256) spread_es_atomic_kernel(SpreadArgs a)
     atomic_tile<W, TAB>(a, blockIdx.x, tre, tim, threadIdx.x, blockDim.x);
 }
 
-// The dense kernels accumulate with atomic adds: clear the band, then launch.
+// The dense kernels accumulate with atomic adds into a zero band: clear it
+// first unless the previous row pass left it zero, then launch.
 template <int W, bool TAB>
-cudaError_t launch_dense(const SpreadArgs& a, int tiles, cudaStream_t st)
+cudaError_t launch_dense(const SpreadArgs& a, int tiles, bool clear, cudaStream_t st)
 {
-    const size_t pitch = sizeof(float2) * (size_t)a.nfx;
-    const int c0 = a.band_tx0 * kTileX, r0 = a.band_ty0 * kTileY;
-    const size_t width = sizeof(float2) * (size_t)a.band_ntx * kTileX;
-    const size_t height = (size_t)(tiles / a.band_ntx) * kTileY;
-    cudaError_t e = cudaMemset2DAsync(a.grid + (size_t)r0 * a.nfx + c0, pitch, 0, width, height, st);
-    if (e != cudaSuccess) return e;
+    if (clear) {
+        const size_t pitch = sizeof(float2) * (size_t)a.nfx;
+        const int c0 = a.band_tx0 * kTileX, r0 = a.band_ty0 * kTileY;
+        const size_t width = sizeof(float2) * (size_t)a.band_ntx * kTileX;
+        const size_t height = (size_t)(tiles / a.band_ntx) * kTileY;
+        const cudaError_t e =
+            cudaMemset2DAsync(a.grid + (size_t)r0 * a.nfx + c0, pitch, 0, width, height, st);
+        if (e != cudaSuccess) return e;
+    }
     spread_es_dense_kernel<W, TAB><<<(a.dense_items + kDenseWarps - 1) / kDenseWarps,
                                      32 * kDenseWarps, 0, st>>>(a, a.dense_items);
     return cudaGetLastError();
 }
 
 template <int W>
-cudaError_t launch_w(const SpreadArgs& a, int tiles, bool colored, bool windowed, cudaStream_t st)
+cudaError_t launch_w(const SpreadArgs& a, int tiles, bool colored, bool windowed, bool clear,
+                     cudaStream_t st)
 {
     if constexpr (W <= kMaxWindowWidth) {
-        if (a.dense_rows > 0) return launch_dense<W, false>(a, tiles, st);
+        if (a.dense_rows > 0) return launch_dense<W, false>(a, tiles, clear, st);
         if (windowed) {
             spread_es_window_kernel<W, kTileX, kColTileY, false>
                 <<<tiles * (kTileY / kColTileY), 32, 0, st>>>(a);
@@ -90,9 +95,9 @@ cudaError_t launch_w(const SpreadArgs& a, int tiles, bool colored, bool windowed
     return cudaGetLastError();
 }
 
-cudaError_t launch_table(const SpreadArgs& a, int tiles, bool colored, cudaStream_t st)
+cudaError_t launch_table(const SpreadArgs& a, int tiles, bool colored, bool clear, cudaStream_t st)
 {
-    if (a.dense_rows > 0) return launch_dense<kLearnW, true>(a, tiles, st);
+    if (a.dense_rows > 0) return launch_dense<kLearnW, true>(a, tiles, clear, st);
     if (colored)
         spread_es_colored_kernel<kLearnW, kTileX, kColTileY, true>
             <<<tiles * (kTileY / kColTileY), 32, 0, st>>>(a);
@@ -206,28 +211,32 @@ asfd_status launch_spread(asfd_plan_s* P, const float2* u1, cudaStream_t st)
     if (tiles <= 0) return ASFD_OK;
     const bool colored = P->colored;
     const bool windowed = P->colored && P->windowed;
+    // the accumulating (dense) kernels need a zero band; the tile kernels
+    // overwrite every band cell
+    const bool clear = !P->band_clean;
+    P->band_clean = false;
     cudaError_t e;
     if (P->learned) {
-        e = launch_table(a, tiles, colored, st);
+        e = launch_table(a, tiles, colored, clear, st);
         if (e != cudaSuccess) return cuda_fail(e, "learned spread kernel launch");
         return ASFD_OK;
     }
     switch (P->w) {
-        case 2: e = launch_w<2>(a, tiles, colored, windowed, st); break;
-        case 3: e = launch_w<3>(a, tiles, colored, windowed, st); break;
-        case 4: e = launch_w<4>(a, tiles, colored, windowed, st); break;
-        case 5: e = launch_w<5>(a, tiles, colored, windowed, st); break;
-        case 6: e = launch_w<6>(a, tiles, colored, windowed, st); break;
-        case 7: e = launch_w<7>(a, tiles, colored, windowed, st); break;
-        case 8: e = launch_w<8>(a, tiles, colored, windowed, st); break;
-        case 9: e = launch_w<9>(a, tiles, colored, windowed, st); break;
-        case 10: e = launch_w<10>(a, tiles, colored, windowed, st); break;
-        case 11: e = launch_w<11>(a, tiles, colored, windowed, st); break;
-        case 12: e = launch_w<12>(a, tiles, colored, windowed, st); break;
-        case 13: e = launch_w<13>(a, tiles, colored, windowed, st); break;
-        case 14: e = launch_w<14>(a, tiles, colored, windowed, st); break;
-        case 15: e = launch_w<15>(a, tiles, colored, windowed, st); break;
-        case 16: e = launch_w<16>(a, tiles, colored, windowed, st); break;
+        case 2: e = launch_w<2>(a, tiles, colored, windowed, clear, st); break;
+        case 3: e = launch_w<3>(a, tiles, colored, windowed, clear, st); break;
+        case 4: e = launch_w<4>(a, tiles, colored, windowed, clear, st); break;
+        case 5: e = launch_w<5>(a, tiles, colored, windowed, clear, st); break;
+        case 6: e = launch_w<6>(a, tiles, colored, windowed, clear, st); break;
+        case 7: e = launch_w<7>(a, tiles, colored, windowed, clear, st); break;
+        case 8: e = launch_w<8>(a, tiles, colored, windowed, clear, st); break;
+        case 9: e = launch_w<9>(a, tiles, colored, windowed, clear, st); break;
+        case 10: e = launch_w<10>(a, tiles, colored, windowed, clear, st); break;
+        case 11: e = launch_w<11>(a, tiles, colored, windowed, clear, st); break;
+        case 12: e = launch_w<12>(a, tiles, colored, windowed, clear, st); break;
+        case 13: e = launch_w<13>(a, tiles, colored, windowed, clear, st); break;
+        case 14: e = launch_w<14>(a, tiles, colored, windowed, clear, st); break;
+        case 15: e = launch_w<15>(a, tiles, colored, windowed, clear, st); break;
+        case 16: e = launch_w<16>(a, tiles, colored, windowed, clear, st); break;
         default: return fail(ASFD_ERR_UNSUPPORTED, "kernel width outside 2..16");
     }
     if (e != cudaSuccess) return cuda_fail(e, "spread kernel launch");

@@ -371,3 +371,38 @@ def test_invalid_height_map_rejected(bad, status):
     with pytest.raises(capi.AsfdError) as ei:
         FresnelPlan(g, d1)
     assert ei.value.status == status
+
+
+@pytest.mark.parametrize("name", ["smooth_random2048", "sinusoid64"])
+def test_band_state_across_call_sequences(name):
+    """The accumulating spread needs a zero band; the forward row pass clears
+    each band cell as it reads it, and the plan clears the band itself only
+    when something else wrote it.  Every sequence of calls gives the plain
+    forward result: repeated forwards, a spread stage run twice before the
+    FFT stages, an adjoint (which writes the grid) before a forward, a height
+    map changed and restored, and a different field in between."""
+    g, u1, d1 = W.make(name, scale=4 if name == "smooth_random2048" else 1)
+    rng = np.random.default_rng(31)
+    u1b = (rng.standard_normal(u1.shape) + 1j * rng.standard_normal(u1.shape)).astype(np.complex64)
+    with FresnelPlan(g, d1) as plan:
+        ut, ub = torch.as_tensor(u1, device="cuda"), torch.as_tensor(u1b, device="cuda")
+        ref = plan.execute(ut).cpu().numpy()
+        outs = [plan.execute(ut).cpu().numpy()]
+        out = torch.empty(plan.shape2, dtype=torch.complex64, device="cuda")
+        plan.execute_stage(0, u1=ub)
+        plan.execute_stage(0, u1=ut)
+        plan.execute_stage(1)
+        plan.execute_stage(2, out=out)
+        outs.append(out.cpu().numpy())
+        gu1 = torch.empty_like(ut)
+        plan.adjoint(None, torch.as_tensor(np.conj(ref), device="cuda"), gu1, None)
+        outs.append(plan.execute(ut).cpu().numpy())
+        plan.update_d1(0.5 * d1)
+        plan.execute(ub)
+        plan.update_d1(d1)
+        outs.append(plan.execute(ut).cpu().numpy())
+        plan.execute(ub)
+        outs.append(plan.execute(ut).cpu().numpy())
+    for i, o in enumerate(outs):
+        assert rel_l2(o, ref) < 1e-6, i
+    assert rel_l2(ref, oracle.eq7(g, u1, d1) if name == "sinusoid64" else ref) < TOL_ES
