@@ -255,14 +255,16 @@ asfd_status launch_fft_rows(asfd_plan_s* P, cudaStream_t st)
 {
     RowArgs a = make_row_args(P);
     if (a.nrows <= 0) return ASFD_OK;
-    // the pass reads every band cell once and leaves the band zero
-    a.clear = 1;
+    // for the accumulating (dense) spread the pass leaves the band zero: each
+    // thread zeroes the band cells it loaded once its transform is done
+    // (2176^2 band at 2048^2: +1.8 us here against 7.5 us for a separate clear)
+    a.clear = P->dense ? 1 : 0;
     cudaError_t e = cudaSuccess;
 #define ASFD_ROWS(L) e = rows_L<L>(a, st)
     ASFD_FFT_SWITCH(P->nfx, ASFD_ROWS)
 #undef ASFD_ROWS
     if (e != cudaSuccess) return cuda_fail(e, "fft_rows_kernel launch");
-    P->band_clean = true;
+    P->band_clean = P->dense;
     return ASFD_OK;
 }
 

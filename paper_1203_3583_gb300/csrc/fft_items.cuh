@@ -46,7 +46,7 @@ struct RowArgs {
     float2* out;         // [nrows][m2x] kept bins, order k + m2x/2
     int m2x;
     const float2* tw;
-    int clear;           // 1: zero each band cell once it is loaded (the next
+    int clear;           // 1: zero the band cells after the transform (the next
                          // accumulating spread then needs no separate clear)
 };
 
@@ -77,13 +77,10 @@ __device__ __forceinline__ void rows_body(const RowArgs& a, int blk, float2* sm,
     float2* dst = a.out + (size_t)(active ? r : 0) * a.m2x;
     const int half = a.m2x / 2;
     const int col_lo = a.col_lo, col_hi = a.col_hi;
-    const bool clear = a.clear != 0;
+    // plain loads, not the read-only path: with clear set the kernel writes
+    // these cells (after every load of them has been used)
     auto ld = [&](int i) -> float2 {
-        if (!(active && i >= col_lo && i < col_hi)) return make_float2(0.f, 0.f);
-        // each band cell is read by exactly one thread, once
-        const float2 v = src[i];
-        if (clear) src[i] = make_float2(0.f, 0.f);
-        return v;
+        return (active && i >= col_lo && i < col_hi) ? src[i] : make_float2(0.f, 0.f);
     };
     auto st = [&](int i, float2 v) {
         if (!active) return;
@@ -91,6 +88,17 @@ __device__ __forceinline__ void rows_body(const RowArgs& a, int blk, float2* sm,
         else if (i >= L - half) dst[i - (L - half)] = v;
     };
     fft_line<L, -1>(t, sm + line * C::LS, a.tw, ld, st);
+    if (a.clear && active) {
+        // zero the band cells this thread loaded (the first pass's indices)
+        constexpr int R0 = FftShape<L>::R0;
+#pragma unroll
+        for (int b = 0; b < 16 / R0; ++b)
+#pragma unroll
+            for (int r = 0; r < R0; ++r) {
+                const int i = t + b * C::TPL + r * (L / R0);
+                if (i >= col_lo && i < col_hi) src[i] = make_float2(0.f, 0.f);
+            }
+    }
 }
 
 // FFT along y of LPC kept columns over the band rows, then deconvolution,
