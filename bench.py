@@ -198,7 +198,8 @@ def stage_bytes(info, g):
 
 STAGE_KERNELS = ["spread", "fft_rows_kernel", "fft_cols_kernel"]
 SPREAD_KERNEL = {0: "spread_es_colored_kernel", 1: "spread_es_atomic_kernel",
-                 2: "spread_es_window_kernel", 3: "spread_es_dense_kernel"}
+                 2: "spread_es_window_kernel", 3: "spread_es_dense_kernel",
+                 4: "spread_item_kernel"}
 # bytes per source sample of the whole forward step in the unpruned model:
 # u1 + d1 (12) + fine-grid write (4 M^2 8 / N^2 = 32) + row read (32) + row write
 # (16) + column read (16) + u2 write (8), sigma = 2 and N = M

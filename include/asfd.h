@@ -107,7 +107,11 @@ typedef struct {
                              /*    2: conflict-free warp tiles with a sliding register  */
                              /*    window per lane (ES widths up to 7); 3: dense maps   */
                              /*    (many samples per cell): register windows flushed    */
-                             /*    to the fine grid with atomic adds (widths up to 7)   */
+                             /*    to the fine grid with atomic adds (widths up to 7);  */
+                             /*    4: deterministic plans whose samples are at least a  */
+                             /*    fine cell apart in x (widths up to 7): register      */
+                             /*    windows flushed into per-item shared-memory tiles in */
+                             /*    a fixed order, then an ordered gather (no atomics)   */
     int stride_x, stride_y;  /* sample strides between lanes of one warp step (0, 2)    */
     int run_rows;            /* source rows per lane run of the register-window spread  */
                              /*    (spread_kind 3; 0 otherwise)                         */

@@ -117,6 +117,14 @@ struct asfd_plan_s {
     bool windowed = false;          // register-window kernel applies (w <= kMaxWindowWidth)
     bool dense = false;             // dense map: register windows flushed with global atomics
     int dense_rows = 0, dense_items = 0;
+    // atomic-free spread through per-item shared-memory tiles and an ordered
+    // gather (deterministic plans whose samples are >= 1 cell apart in x)
+    bool itemtile = false;
+    int it_rows = 0, it_items = 0, it_ncb = 0, it_tw = 0, it_th = 0;
+    int* it_xbox = nullptr;         // [column blocks][2] first tap column range
+    int* it_ybox = nullptr;         // [runs][2] first tap row range
+    int* it_xmap = nullptr;         // [band columns] first covering block | count << 24
+    int* it_ymap = nullptr;         // [band rows] first covering run | count << 24
     int sx_min = 0, h_min = 0, sxw_min = 0;
     double min_step_x = 0.0, min_step_y = 0.0, row_spread_y = 0.0, col_spread_x = 0.0;
     long long tile_pairs = 0;
@@ -181,6 +189,9 @@ void clear_error();
 
 // stage launchers (each returns ASFD_OK or an error with a message)
 asfd_status launch_spread(asfd_plan_s* P, const float2* u1, cudaStream_t st);
+// deterministic item-tile spread (spread_item.cu): plan set-up and launch
+asfd_status plan_build_itemtile(asfd_plan_s* P, cudaStream_t st);
+asfd_status launch_spread_itemtile(asfd_plan_s* P, const float2* u1, cudaStream_t st);
 // dense plans: add the spread of u1 into `grid` (not cleared; another plan's grid)
 asfd_status launch_spread_into(asfd_plan_s* P, const float2* u1, float2* grid, cudaStream_t st);
 // row / column passes over the band rows [ty0, ty1) (and columns [tx0, tx1)) in tiles

@@ -279,7 +279,8 @@ asfd_status asfd_get_plan_info(asfd_plan P, asfd_plan_info* info)
     info->es_beta = P->beta;
     info->max_abs_eps = P->max_abs_eps;
     info->device_bytes = P->device_bytes;
-    info->spread_kind = P->colored ? (P->windowed && !P->learned ? 2 : 0) : (P->dense ? 3 : 1);
+    info->spread_kind = P->itemtile ? 4
+                      : P->colored ? (P->windowed && !P->learned ? 2 : 0) : (P->dense ? 3 : 1);
     info->stride_x = info->spread_kind == 2 ? P->sxw_min : P->sx_min;
     info->stride_y = P->h_min;
     info->run_rows = P->dense ? P->dense_rows : 0;

@@ -708,6 +708,7 @@ asfd_status plan_build_colored(asfd_plan_s* P, bool wraps, cudaStream_t st)
     P->colored = false;
     P->windowed = false;
     P->dense = false;
+    P->itemtile = false;
     min_step_kernel<<<kStepBlocks, 256, 0, st>>>(P->q, P->ax, P->ay, P->bux, P->buy, p.n1x, p.n1y,
                                                  P->step_min);
     ASFD_CUDA(cudaGetLastError());
@@ -818,7 +819,9 @@ asfd_status plan_build_colored(asfd_plan_s* P, bool wraps, cudaStream_t st)
         P->sxw_min = (int)sxw;
         P->windowed = true;
     }
-    return ASFD_OK;
+    // the faster atomic-free path where it applies (the tiles above stay
+    // built: the batched kernel uses them)
+    return plan_build_itemtile(P, st);
 }
 
 }  // namespace asfd

@@ -215,6 +215,7 @@ asfd_status launch_spread(asfd_plan_s* P, const float2* u1, cudaStream_t st)
     // overwrite every band cell
     const bool clear = !P->band_clean;
     P->band_clean = false;
+    if (P->itemtile) return launch_spread_itemtile(P, u1, st);
     cudaError_t e;
     if (P->learned) {
         e = launch_table(a, tiles, colored, clear, st);
