@@ -40,6 +40,7 @@ namespace {
 constexpr int kItemWarps = 4;                 // warps (items) per block
 constexpr int kItemMaxTileBytes = 18 * 1024;  // shared-memory tile per warp, at most
 constexpr int kItemMaxOverlap = 3;            // column blocks (runs) covering one fine column (row)
+constexpr int kItemMinRows = 8;               // shortest runs tried
 
 struct ItemArgs {
     SpreadArgs s;
@@ -250,16 +251,15 @@ asfd_status plan_build_itemtile(asfd_plan_s* P, cudaStream_t st)
     long long slots = 0;
     asfd_status s = item_slots(P->w, &slots);
     if (s != ASFD_OK) return s;
-    const int rows = window_run_rows(p.n1y, ncb, slots);
-    const long long nruns = (p.n1y + rows - 1) / rows;
-    const long long items = ncb * nruns;
-    // tables: per column block, per run and per fine column / row (sizes fixed
-    // by the plan's grids; each allocated once, a refused one retried later)
+    const int rows0 = window_run_rows(p.n1y, ncb, slots);
+    // tables: per column block, per run (sized for the shortest runs tried)
+    // and per fine column / row; each allocated once, a refused one retried
+    const long long max_runs = (p.n1y + kItemMinRows - 1) / kItemMinRows;
     const struct {
         int** ptr;
         size_t bytes;
     } tabs[] = {{&P->it_xbox, sizeof(int) * 2 * ncb},
-                {&P->it_ybox, sizeof(int) * 2 * nruns},
+                {&P->it_ybox, sizeof(int) * 2 * max_runs},
                 {&P->it_xmap, sizeof(int) * P->nfx},
                 {&P->it_ymap, sizeof(int) * P->nfy}};
     for (const auto& t : tabs)
@@ -268,23 +268,36 @@ asfd_status plan_build_itemtile(asfd_plan_s* P, cudaStream_t st)
             *t.ptr = nullptr;
             return s;
         }
-    item_box_init_kernel<<<(unsigned)((2 * ncb + 255) / 256), 256, 0, st>>>(P->it_xbox, (int)(2 * ncb));
-    item_box_init_kernel<<<(unsigned)((2 * nruns + 255) / 256), 256, 0, st>>>(P->it_ybox, (int)(2 * nruns));
+    // runs of the wave rule's length, halved until an item's tile fits the
+    // shared memory of a warp and all tiles fit the row buffer
     SpreadArgs a = make_spread_args(P, nullptr);
-    item_box_kernel<<<1024, 256, 0, st>>>(a, rows, P->it_xbox, P->it_ybox);
-    ASFD_CUDA(cudaGetLastError());
-    std::vector<int> xb(2 * ncb), yb(2 * nruns);
-    ASFD_CUDA(cudaMemcpyAsync(xb.data(), P->it_xbox, sizeof(int) * xb.size(), cudaMemcpyDeviceToHost, st));
-    ASFD_CUDA(cudaMemcpyAsync(yb.data(), P->it_ybox, sizeof(int) * yb.size(), cudaMemcpyDeviceToHost, st));
-    ASFD_CUDA(cudaStreamSynchronize(st));
-    int tw = 0, th = 0;
-    for (long long c = 0; c < ncb; ++c) tw = std::max(tw, xb[2 * c + 1] - xb[2 * c]);
-    for (long long r = 0; r < nruns; ++r) th = std::max(th, yb[2 * r + 1] - yb[2 * r]);
-    // the tile must fit the shared memory the occupancy was sized for, and the
-    // scratch (all items' tiles) the row buffer it borrows
-    if (tw <= 0 || th <= 0 || (long long)tw * th * (long long)sizeof(float2) > kItemMaxTileBytes)
-        return ASFD_OK;
-    if ((double)items * tw * th > (double)P->nfy * p.m2x) return ASFD_OK;
+    int rows = rows0, tw = 0, th = 0;
+    long long nruns = 0, items = 0;
+    std::vector<int> xb(2 * ncb), yb;
+    for (;; rows = (rows + 1) / 2) {
+        if (rows < kItemMinRows) return ASFD_OK;
+        nruns = (p.n1y + rows - 1) / rows;
+        items = ncb * nruns;
+        item_box_init_kernel<<<(unsigned)((2 * ncb + 255) / 256), 256, 0, st>>>(P->it_xbox,
+                                                                               (int)(2 * ncb));
+        item_box_init_kernel<<<(unsigned)((2 * nruns + 255) / 256), 256, 0, st>>>(P->it_ybox,
+                                                                                 (int)(2 * nruns));
+        item_box_kernel<<<1024, 256, 0, st>>>(a, rows, P->it_xbox, P->it_ybox);
+        ASFD_CUDA(cudaGetLastError());
+        yb.assign(2 * nruns, 0);
+        ASFD_CUDA(cudaMemcpyAsync(xb.data(), P->it_xbox, sizeof(int) * xb.size(),
+                                  cudaMemcpyDeviceToHost, st));
+        ASFD_CUDA(cudaMemcpyAsync(yb.data(), P->it_ybox, sizeof(int) * yb.size(),
+                                  cudaMemcpyDeviceToHost, st));
+        ASFD_CUDA(cudaStreamSynchronize(st));
+        tw = th = 0;
+        for (long long c = 0; c < ncb; ++c) tw = std::max(tw, xb[2 * c + 1] - xb[2 * c]);
+        for (long long r = 0; r < nruns; ++r) th = std::max(th, yb[2 * r + 1] - yb[2 * r]);
+        if (tw <= 0 || th <= 0) return ASFD_OK;
+        if ((long long)tw * th * (long long)sizeof(float2) > kItemMaxTileBytes) continue;
+        if ((double)items * tw * th > (double)P->nfy * p.m2x) return ASFD_OK;
+        break;
+    }
     // per band column: the column blocks whose box covers it (consecutive,
     // since the boxes move monotonically with the block); likewise per band row
     const int bx0 = P->band_tx0 * kTileX, bx1 = P->band_tx1 * kTileX;
