@@ -106,9 +106,12 @@ __device__ __forceinline__ void item_tile(const ItemArgs& ia, int it, int lane, 
     int X0 = 0, R0 = 0;
     bool live = false;
     // rows b < nflush of the window go to the tile, in warp-uniform phases
+    // (as many rows as the lane that flushes most: usually one or two)
     auto flush = [&](int nflush) {
+        const int nb = __reduce_max_sync(wmask, lane_on ? nflush : 0);
 #pragma unroll
         for (int b = 0; b < W; ++b) {
+            if (b >= nb) break;  // warp-uniform
             const int r = R0 + b - ylo;
             const bool on = lane_on && b < nflush && (unsigned)r < (unsigned)th;
 #pragma unroll
