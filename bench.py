@@ -205,15 +205,16 @@ SPREAD_KERNEL = {0: "spread_es_colored_kernel", 1: "spread_es_atomic_kernel",
 # (16) + column read (16) + u2 write (8), sigma = 2 and N = M
 STEP_BYTES_PER_SAMPLE = 116
 # DRAM bytes (read + write) per launch of the dominant kernel from one ncu
-# capture, with the SHA-1 of the kernel's sources at the time of the capture:
-# the traffic is reported only while the sources still hash to that state (a
-# kernel changed since its capture, or without one, reports null)
-SPREAD_SOURCES = ("paper_1203_3583_gb300/csrc/spread.cuh", "paper_1203_3583_gb300/csrc/sample.cuh",
-                  "paper_1203_3583_gb300/csrc/spread.cu")
+# capture, with the SHA-1 of the kernel's code (the files that define it and
+# the per-sample arithmetic it inlines) and its launch grid at the time of the
+# capture: the traffic is reported only while both are unchanged (a kernel
+# changed since its capture, or without one, reports null)
+SPREAD_SOURCES = ("paper_1203_3583_gb300/csrc/spread.cuh", "paper_1203_3583_gb300/csrc/sample.cuh")
 NCU_TRAFFIC = {("spread_es_dense_kernel<7>", "smooth_random2048"): {
     "bytes": 86.784000e6 + 1.624832e6,
+    "grid": 912,
     "capture": "profiles/spread_es_dense_w7_smooth_random2048.md",
-    "sources_sha1": "5d95bda3a58878ed4059bce170a3c53357ffb26a"}}
+    "sources_sha1": "025f3964b6ff962a8ece156c70b2c7dcb768ebdb"}}
 
 
 def sources_sha1(paths) -> str:
@@ -225,14 +226,17 @@ def sources_sha1(paths) -> str:
     return h.hexdigest()
 
 
-def captured_traffic(kernel: str, workload: str):
+def captured_traffic(kernel: str, workload: str, grid: int):
     """(DRAM bytes per launch or None, provenance note)."""
     rec = NCU_TRAFFIC.get((kernel, workload))
     if rec is None:
         return None, "no ncu capture of this kernel and workload"
     if sources_sha1(SPREAD_SOURCES) != rec["sources_sha1"]:
         return None, f"kernel sources changed since the capture in {rec['capture']}"
-    return rec["bytes"], f"ncu capture in {rec['capture']} (sources sha1 {rec['sources_sha1'][:12]})"
+    if grid != rec["grid"]:
+        return None, f"launch grid {grid} differs from the capture's {rec['grid']}"
+    return rec["bytes"], (f"ncu capture in {rec['capture']} (sources sha1 "
+                          f"{rec['sources_sha1'][:12]}, grid {grid})")
 
 
 def oracle_sample(g, u1, d1, seconds, seed=7):
@@ -371,7 +375,9 @@ def run_ours(args):
     peak, peak_src = measured_peaks()
     achieved = sb[dom] / (mean_stage[dom] * 1e-3) / 1e9
     names = [f"{SPREAD_KERNEL[info['spread_kind']]}<{args.width}>"] + STAGE_KERNELS[1:]
-    traffic, traffic_src = captured_traffic(names[dom], args.workload)
+    # launch grid of the dense spread: warp items of 32 columns x run_rows rows, 4 per block
+    n_items = -(-g["n1x"] // 32) * -(-g["n1y"] // max(1, info["run_rows"]))
+    traffic, traffic_src = captured_traffic(names[dom], args.workload, -(-n_items // 4))
     roofline = {"bound": "hbm", "kernel": names[dom], "achieved": achieved, "peak": peak,
                 "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "traffic_source": traffic_src,
