@@ -246,3 +246,20 @@ def test_workspace_bytes_without_gpu(lib_path):
     assert b"even" in lib.asfd_last_error()
     assert lib.asfd_workspace_bytes(None) == 0
     assert lib.asfd_set_workspace(None, None, 0) == 1
+
+
+def test_probe_argument_checks_without_gpu(lib_path):
+    """The resource probes check their arguments before any device call."""
+    import ctypes
+    from paper_1203_3583_gb300 import capi
+    lib = capi.load(lib_path)
+    work = ctypes.c_double(-1.0)
+    fake = ctypes.c_void_p(256)
+    assert lib.asfd_probe_launch(capi.PROBES["ffma2"], 1, fake, 0, None, None) == 1
+    assert lib.asfd_probe_launch(capi.PROBES["ffma2"], 1, None, 1024, ctypes.byref(work), None) == 1
+    assert lib.asfd_probe_launch(capi.PROBES["ffma2"], 0, fake, 1024, ctypes.byref(work), None) == 1
+    assert lib.asfd_probe_launch(capi.PROBES["ffma2"], (1 << 20) + 1, fake, 1024,
+                                 ctypes.byref(work), None) == 1
+    assert lib.asfd_probe_launch(99, 1, fake, 1024, ctypes.byref(work), None) == 1
+    assert b"unknown probe" in lib.asfd_last_error()
+    assert work.value == -1.0
