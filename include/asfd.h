@@ -199,6 +199,21 @@ asfd_status asfd_execute(asfd_plan plan, const float* u1_dev, float* u2_dev, voi
 asfd_status asfd_execute_host(asfd_plan plan, const float* u1_host, float* u2_host, void* stream);
 
 /*
+ * asfd_execute_host without the final synchronisation: the transform, its
+ * host-link reads of u1 and its copies of u2 are queued on `stream` (the
+ * copies of u2's column blocks on a stream of the plan that `stream` waits
+ * for), and the call returns.  The host buffers must stay valid, u1
+ * unchanged and u2 unread, until `stream` reaches this point.  With
+ * page-locked buffers the call does not block, so transforms on two plans
+ * and two streams overlap one's copies of u2 with the other's reads of u1
+ * (the host link carries both directions at once); one plan serves one
+ * stream at a time.  A pageable u2 makes the call wait for its copy.
+ * Errors: as asfd_execute_host.
+ */
+asfd_status asfd_execute_host_async(asfd_plan plan, const float* u1_host, float* u2_host,
+                                    void* stream);
+
+/*
  * One stage of asfd_execute, for per-kernel timing with events recorded on
  * `stream` between the calls:
  *   stage 0: per-sample prefactor + tiled spread: reads u1_dev, writes the

@@ -107,6 +107,7 @@ SIGNATURES = {
     "asfd_set_workspace": (_int, [_vp, _vp, ctypes.c_size_t]),
     "asfd_execute": (_int, [_vp, _vp, _vp, _vp]),
     "asfd_execute_host": (_int, [_vp, _vp, _vp, _vp]),
+    "asfd_execute_host_async": (_int, [_vp, _vp, _vp, _vp]),
     "asfd_execute_stage": (_int, [_vp, _int, _vp, _vp, _vp]),
     "asfd_adjoint": (_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
     "asfd_get_plan_info": (_int, [_vp, ctypes.POINTER(PlanInfo)]),
@@ -326,14 +327,18 @@ def asfd_adjoint(plan, u1, grad_u2, grad_u1, grad_d1, shape1, shape2, stream=Non
     _check(lib.asfd_adjoint(plan, p_u1, p_g2, p_g1, p_gd, _stream(stream)))
 
 
-def asfd_execute_host(plan, u1: torch.Tensor, u2: torch.Tensor, shape1, shape2, stream=None) -> None:
+def asfd_execute_host(plan, u1: torch.Tensor, u2: torch.Tensor, shape1, shape2, stream=None,
+                      sync: bool = True) -> None:
+    """sync=False calls asfd_execute_host_async: the host tensors must stay
+    alive and untouched until the stream reaches the transform."""
     lib = load()
     for t, name, shape in ((u1, "u1", shape1), (u2, "u2", shape2)):
         if t.is_cuda or t.dtype != torch.complex64 or tuple(t.shape) != tuple(shape) \
                 or not t.is_contiguous():
             raise ValueError(f"{name} must be a contiguous complex64 host tensor of shape {shape}")
-    _check(lib.asfd_execute_host(plan, ctypes.c_void_p(u1.data_ptr()),
-                                 ctypes.c_void_p(u2.data_ptr()), _stream(stream)))
+    fn = lib.asfd_execute_host if sync else lib.asfd_execute_host_async
+    _check(fn(plan, ctypes.c_void_p(u1.data_ptr()), ctypes.c_void_p(u2.data_ptr()),
+              _stream(stream)))
 
 
 def asfd_get_plan_info(plan) -> dict:

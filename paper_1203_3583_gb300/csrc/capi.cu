@@ -199,7 +199,9 @@ asfd_status asfd_adjoint(asfd_plan P, const float* u1_dev, const float* grad_u2_
     });
 }
 
-asfd_status asfd_execute_host(asfd_plan P, const float* u1_host, float* u2_host, void* stream)
+// Queues the host-buffer transform on `stream`; `sync` waits for it.
+static asfd_status execute_host(asfd_plan P, const float* u1_host, float* u2_host, void* stream,
+                                bool sync)
 {
     clear_error();
     if (!P || !u1_host || !u2_host) return fail(ASFD_ERR_ARG, "plan, u1 or u2 is NULL");
@@ -256,9 +258,19 @@ asfd_status asfd_execute_host(asfd_plan P, const float* u1_host, float* u2_host,
             ASFD_CUDA(cudaEventRecord(P->copy_ev[kHostColBlocks], P->copy_stream));
             ASFD_CUDA(cudaStreamWaitEvent(st, P->copy_ev[kHostColBlocks], 0));
         }
-        ASFD_CUDA(cudaStreamSynchronize(st));
+        if (sync) ASFD_CUDA(cudaStreamSynchronize(st));
         return ASFD_OK;
     });
+}
+
+asfd_status asfd_execute_host(asfd_plan P, const float* u1_host, float* u2_host, void* stream)
+{
+    return execute_host(P, u1_host, u2_host, stream, true);
+}
+
+asfd_status asfd_execute_host_async(asfd_plan P, const float* u1_host, float* u2_host, void* stream)
+{
+    return execute_host(P, u1_host, u2_host, stream, false);
 }
 
 asfd_status asfd_get_plan_info(asfd_plan P, asfd_plan_info* info)

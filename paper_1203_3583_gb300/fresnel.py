@@ -92,8 +92,12 @@ class FresnelPlan:
             return FresnelFunction.apply(u1, d1, self)
         return FresnelFunction.apply(u1, None, self)
 
-    def execute_host(self, u1: torch.Tensor, out: torch.Tensor, stream=None) -> torch.Tensor:
-        capi.asfd_execute_host(self.handle, u1, out, self.shape1, self.shape2, stream)
+    def execute_host(self, u1: torch.Tensor, out: torch.Tensor, stream=None,
+                     sync: bool = True) -> torch.Tensor:
+        """Transform host tensors (page-locked ones are read and written over
+        the host link while the kernels run).  sync=False only queues the
+        work on `stream`: keep u1 and out untouched until it completes."""
+        capi.asfd_execute_host(self.handle, u1, out, self.shape1, self.shape2, stream, sync)
         return out
 
     def info(self) -> dict:

@@ -263,3 +263,15 @@ def test_probe_argument_checks_without_gpu(lib_path):
     assert lib.asfd_probe_launch(99, 1, fake, 1024, ctypes.byref(work), None) == 1
     assert b"unknown probe" in lib.asfd_last_error()
     assert work.value == -1.0
+
+
+def test_host_execute_checks_without_gpu(lib_path):
+    """NULL plans and buffers are refused before any device call."""
+    import ctypes
+    from paper_1203_3583_gb300 import capi
+    lib = capi.load(lib_path)
+    fake = ctypes.c_void_p(256)
+    for fn in (lib.asfd_execute_host, lib.asfd_execute_host_async):
+        assert fn(None, fake, fake, None) == 1
+        assert fn(fake, None, fake, None) == 1
+        assert fn(fake, fake, None, None) == 1
