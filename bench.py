@@ -413,22 +413,22 @@ def run_ours(args):
         e2e_t.append(time.perf_counter() - t)
     e2e_s = max_over_ranks(statistics.mean(e2e_t), dev, world)
     serial_value = whole_job_rate(n_src, world, e2e_s)
-    # a stream of transforms: two plans on two streams take alternate steps,
+    # a stream of transforms: E2E_PLANS plans on as many streams take turns,
     # each step queued with asfd_execute_host_async, so that one step's
-    # copies of u2 to the host overlap the next step's reads of u1
+    # copies of u2 to the host overlap the next steps' uploads and kernels
     pipe_s = max_over_ranks(e2e_pipelined(g, d1, args, plan, hu1, hu2), dev, world)
     pipe_value = whole_job_rate(n_src, world, pipe_s)
     e2e = {"value": pipe_value, "unit": UNIT,
            "h2d_bytes_per_step": hu1.numel() * 8,
            "d2h_bytes_per_step": hu2.numel() * 8,
-           "path": "page-locked host buffers: u1 read by the spread in place over the host "
-                   "link; u2 copied to the host in four column blocks, each while the column "
-                   "pass transforms the next; steps alternate between two plans on two "
-                   "streams (asfd_execute_host_async), one synchronisation after the last "
-                   "(each plan's 139 MB of work buffers exceed L2 between its steps)",
+           "path": f"page-locked host buffers, steps queued with asfd_execute_host_async "
+                   f"on {E2E_PLANS} plans and streams in turn, one synchronisation after the "
+                   "last: u1 uploaded by a copy, u2 copied to the host in four column "
+                   "blocks, each while the column pass transforms the next (each plan's "
+                   "work buffers, 268 MB, exceed L2 between its steps)",
            "serial_value": serial_value,
-           "serial_path": "one asfd_execute_host call at a time (synchronous), L2 flushed "
-                          "before each"}
+           "serial_path": "one asfd_execute_host call at a time (synchronous, u1 read by the "
+                          "spread in place over the host link), L2 flushed before each"}
     # context: pageable host buffers, staged through device copies by the library
     pu1 = torch.as_tensor(u1).clone()
     pu2 = torch.empty(plan.shape2, dtype=torch.complex64)
@@ -478,28 +478,37 @@ def run_ours(args):
     return 0
 
 
+# transforms in flight in the pipelined end-to-end measurement: at 2048^2
+# two leave the host link idle between steps, three keep it busy (four
+# measure the same)
+E2E_PLANS = 3
+
+
 def e2e_pipelined(g, d1, args, plan, hu1, hu2):
     """Seconds per step of `args.steps` host-buffer transforms queued back to
-    back on two plans and two streams (after `args.warmup` untimed ones)."""
+    back, step k on plan k mod E2E_PLANS and its own stream (after
+    `args.warmup` untimed ones)."""
+    import torch
     from paper_1203_3583_gb300.fresnel import FresnelPlan
-    plans = [plan, FresnelPlan(g, d1, kernel_width=args.width)]
+    plans = [plan] + [FresnelPlan(g, d1, kernel_width=args.width) for _ in range(E2E_PLANS - 1)]
     streams = [torch.cuda.Stream() for _ in plans]
-    hin = [hu1, hu1.clone().pin_memory()]
-    hout = [hu2, torch.empty_like(hu2).pin_memory()]
+    hin = [hu1] + [hu1.clone().pin_memory() for _ in plans[1:]]
+    hout = [hu2] + [torch.empty_like(hu2).pin_memory() for _ in plans[1:]]
 
     def run(n):
         for k in range(n):
-            j = k % 2
+            j = k % len(plans)
             plans[j].execute_host(hin[j], hout[j], stream=streams[j], sync=False)
         torch.cuda.synchronize()
 
     try:
-        run(max(2, args.warmup))
+        run(max(len(plans), args.warmup))
         t = time.perf_counter()
         run(args.steps)
         return (time.perf_counter() - t) / args.steps
     finally:
-        plans[1].close()
+        for p in plans[1:]:
+            p.close()
 
 
 def time_device_ms(fn, steps, warmup, flush, stream):

@@ -199,15 +199,17 @@ asfd_status asfd_execute(asfd_plan plan, const float* u1_dev, float* u2_dev, voi
 asfd_status asfd_execute_host(asfd_plan plan, const float* u1_host, float* u2_host, void* stream);
 
 /*
- * asfd_execute_host without the final synchronisation: the transform, its
- * host-link reads of u1 and its copies of u2 are queued on `stream` (the
- * copies of u2's column blocks on a stream of the plan that `stream` waits
- * for), and the call returns.  The host buffers must stay valid, u1
- * unchanged and u2 unread, until `stream` reaches this point.  With
- * page-locked buffers the call does not block, so transforms on two plans
- * and two streams overlap one's copies of u2 with the other's reads of u1
- * (the host link carries both directions at once); one plan serves one
- * stream at a time.  A pageable u2 makes the call wait for its copy.
+ * asfd_execute_host without the final synchronisation: the copy of u1 to
+ * the plan's staging buffer, the transform and the copies of u2 are queued
+ * on `stream` (the copies of u2's column blocks on a stream of the plan that
+ * `stream` waits for), and the call returns.  u1 is copied by the copy
+ * engine, not read in place, so that the SMs stay free for transforms on
+ * other streams.  The host buffers must stay valid, u1 unchanged and u2
+ * unread, until `stream` reaches this point.  With page-locked buffers the
+ * call does not block, so transforms on two plans and two streams overlap
+ * one's copies of u2 with the other's upload of u1 and its kernels (the
+ * host link carries both directions at once); one plan serves one stream
+ * at a time.  A pageable u2 makes the call wait for its copy.
  * Errors: as asfd_execute_host.
  */
 asfd_status asfd_execute_host_async(asfd_plan plan, const float* u1_host, float* u2_host,

@@ -207,15 +207,18 @@ static asfd_status execute_host(asfd_plan P, const float* u1_host, float* u2_hos
     if (!P || !u1_host || !u2_host) return fail(ASFD_ERR_ARG, "plan, u1 or u2 is NULL");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     return on_device(P->device, [&]() -> asfd_status {
-        // u1 in page-locked host memory is read by the spread in place, over
-        // the host link, while it computes (as fast as a copy, and hidden
-        // behind the spread); pageable u1 is copied to the plan's staging
-        // buffer first.  u2 is written to the staging buffer by the column
+        // A synchronous call reads a page-locked u1 in place: the spread
+        // reads it over the host link while it computes (as fast as a copy,
+        // and hidden behind the spread).  A queued call, and any call with a
+        // pageable u1, copies u1 to the plan's staging buffer first: the copy
+        // engine then carries the upload and leaves the SMs to transforms
+        // running on other streams.  u2 is written to the staging buffer by the column
         // pass, in column blocks, and each block is copied to the host while
         // the next one is transformed (the link takes these copies faster
         // than kernel stores to host memory).  Staging buffers are work
         // buffers (the plan's own, allocated on first use, or the workspace).
-        const float2* in = static_cast<const float2*>(mapped_host_address(u1_host));
+        const float2* in = sync ? static_cast<const float2*>(mapped_host_address(u1_host))
+                                : nullptr;
         const bool out_locked = mapped_host_address(u2_host) != nullptr;
         const int m2x = P->prm.m2x, m2y = P->prm.m2y;
         const size_t b1 = sizeof(float2) * (size_t)P->prm.n1x * P->prm.n1y;
