@@ -579,7 +579,7 @@ def resource_fractions(info, g, width, stage_ms, peaks):
     (measured peaks), beside its HBM fraction: the spread's packed FP32 FMA
     (4 W^2 flops per sample), MUFU (4 W evaluations per sample: an exp2 and a
     reciprocal square root per tap and axis) and L2 float2 reductions (window
-    rows flushed: per source column alpha_y n1y + W rows per run, W + 1 cells
+    rows flushed: per source column alpha_y n1y + W rows per run, W cells
     each); the FFT passes' shared-memory exchanges ((passes - 1) stores and
     loads of every line)."""
     import math
@@ -587,7 +587,7 @@ def resource_fractions(info, g, width, stage_ms, peaks):
     nfx, nfy = info["nfx"], info["nfy"]
     alpha_y = g["p1y"] * g["p2y"] * nfy / (g["lam"] * g["z0"])
     runs = max(1, math.ceil(g["n1y"] / max(1, info["run_rows"] or g["n1y"])))
-    flushed = g["n1x"] * (alpha_y * g["n1y"] + runs * width) * (width + 1) * 8.0
+    flushed = g["n1x"] * (alpha_y * g["n1y"] + runs * width) * width * 8.0
     t_sp, t_r, t_c = (ms * 1e-3 for ms in stage_ms)
 
     def smem_bytes(L, lines):
