@@ -97,7 +97,8 @@ typedef struct {
     int band_x0, band_x1;    /* touched fine-grid columns [x0, x1) (storage coords)     */
     int band_y0, band_y1;    /* touched fine-grid rows    [y0, y1)                      */
     int spread_tiles;        /* output tiles the spreading kernel processes             */
-    long long tile_pairs;    /* (output tile, source tile) pairs in the binning         */
+    long long tile_pairs;    /* (output tile, source tile) pairs in the binning of the  */
+                             /*    shared-memory-atomic spread (spread_kind 1; else 0)  */
     double es_beta;          /* ES beta in use                                          */
     double max_abs_eps;      /* max |d1| / z0 over the surface                          */
     size_t device_bytes;     /* device memory owned by the plan                         */

@@ -84,31 +84,35 @@ __global__ void dest_table_kernel(float2* C, int m, double p2, double lam_z0, in
     C[k] = make_float2((float)re, (float)im);
 }
 
-// Checks d1 (finite, below z0) and reduces max |d1|/z0.
-__global__ void d1_check_kernel(const double* d1, size_t n, double z0, unsigned* status,
-                                unsigned* maxeps_bits)
+// Checks d1 (finite, below z0) and reduces max |d1|/z0 (in FP32: a bound
+// checked against 0.1).
+__global__ void d1_check_kernel(const double* d1, size_t n, double z0, float inv_z0,
+                                unsigned* status, unsigned* maxeps_bits)
 {
     const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     float e = 0.f;
     if (i < n) {
         const double h = d1[i];
         if (!isfinite(h) || !(h < z0)) atomicOr(status, kStatusBadD1);
-        else e = (float)(fabs(h) / z0);
+        else e = (float)fabs(h) * inv_z0;
     }
     for (int o = 16; o > 0; o >>= 1) e = fmaxf(e, __shfl_xor_sync(0xffffffffu, e, o));
     if ((threadIdx.x & 31) == 0) atomicMax(maxeps_bits, __float_as_uint(e));
 }
 
-// q = d1 / (z0 - d1) in FP64, stored FP32.
+// q = d1 / (z0 - d1), stored FP32: z0 - d1 formed in FP64 (no cancellation
+// error), both operands rounded to FP32 and divided there (within 1.5 FP32
+// ulp of the FP64 quotient; an FP64 division per sample is slow on this GPU).
 __global__ void d1_q_kernel(const double* d1, float* q, size_t n, double z0)
 {
     const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const double h = d1[i];
-    q[i] = (float)(h / (z0 - h));
+    q[i] = __fdiv_rn((float)h, (float)(z0 - h));
 }
 
-// Per source tile: bounds of the unreduced storage coordinate alpha x~ (1+q) + nf/2.
+// Per source tile: bounds of the unreduced storage coordinate alpha x~ (1+q) + nf/2,
+// in FP32 (within a few 1e-3 cells: the binning adds a one-cell margin).
 __global__ void src_bbox_kernel(const float* q, const AxisEntry* ax, const AxisEntry* ay,
                                 const double* bux, const double* buy, int n1x, int n1y, int nstx,
                                 double4* bbox)
@@ -116,21 +120,21 @@ __global__ void src_bbox_kernel(const float* q, const AxisEntry* ax, const AxisE
     const int tile = blockIdx.x;
     const int nx = (tile % nstx) * kSrcTile + threadIdx.x % kSrcTile;
     const int ny = (tile / nstx) * kSrcTile + threadIdx.x / kSrcTile;
-    double x0 = 1e300, x1 = -1e300, y0 = 1e300, y1 = -1e300;
+    float x0 = 3e38f, x1 = -3e38f, y0 = 3e38f, y1 = -3e38f;
     if (nx < n1x && ny < n1y) {
         const float qq = q[(size_t)ny * n1x + nx];
-        const double ux = bux[nx] + (double)(ax[nx].s * qq);
-        const double uy = buy[ny] + (double)(ay[ny].s * qq);
+        const float ux = (float)bux[nx] + ax[nx].s * qq;
+        const float uy = (float)buy[ny] + ay[ny].s * qq;
         x0 = x1 = ux;
         y0 = y1 = uy;
     }
     for (int o = 16; o > 0; o >>= 1) {
-        x0 = fmin(x0, __shfl_xor_sync(0xffffffffu, x0, o));
-        x1 = fmax(x1, __shfl_xor_sync(0xffffffffu, x1, o));
-        y0 = fmin(y0, __shfl_xor_sync(0xffffffffu, y0, o));
-        y1 = fmax(y1, __shfl_xor_sync(0xffffffffu, y1, o));
+        x0 = fminf(x0, __shfl_xor_sync(0xffffffffu, x0, o));
+        x1 = fmaxf(x1, __shfl_xor_sync(0xffffffffu, x1, o));
+        y0 = fminf(y0, __shfl_xor_sync(0xffffffffu, y0, o));
+        y1 = fmaxf(y1, __shfl_xor_sync(0xffffffffu, y1, o));
     }
-    __shared__ double red[4][kSrcTile * kSrcTile / 32];
+    __shared__ float red[4][kSrcTile * kSrcTile / 32];
     const int wid = threadIdx.x / 32;
     if ((threadIdx.x & 31) == 0) {
         red[0][wid] = x0;
@@ -141,30 +145,52 @@ __global__ void src_bbox_kernel(const float* q, const AxisEntry* ax, const AxisE
     __syncthreads();
     if (threadIdx.x == 0) {
         for (int w = 1; w < kSrcTile * kSrcTile / 32; ++w) {
-            x0 = fmin(x0, red[0][w]);
-            x1 = fmax(x1, red[1][w]);
-            y0 = fmin(y0, red[2][w]);
-            y1 = fmax(y1, red[3][w]);
+            x0 = fminf(x0, red[0][w]);
+            x1 = fmaxf(x1, red[1][w]);
+            y0 = fminf(y0, red[2][w]);
+            y1 = fmaxf(y1, red[3][w]);
         }
         bbox[tile] = make_double4(x0, x1, y0, y1);
     }
 }
 
-// Per source column: [min, max] over rows of the unreduced x storage coordinate.
-__global__ void col_range_kernel(const float* q, const AxisEntry* ax, const double* bux, int n1x,
-                                 int n1y, double2* out)
+// The storage coordinate of a sample is b + (double)(s * q) with b and s
+// fixed per column (x) or per row (y); an FP32 product with a fixed factor
+// and the FP64 sum with a fixed term are monotone in q, so its extremes over
+// a column (row) are those of q, mapped.
+__device__ __forceinline__ double2 coord_range(double b, float s, float qlo, float qhi)
 {
-    const int nx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (nx >= n1x) return;
-    const double b = bux[nx];
-    const float s = ax[nx].s;
-    double lo = 1e300, hi = -1e300;
-    for (int ny = 0; ny < n1y; ++ny) {
-        const double g = b + (double)(s * q[(size_t)ny * n1x + nx]);
-        lo = fmin(lo, g);
-        hi = fmax(hi, g);
+    const float a0 = s * qlo, a1 = s * qhi;
+    return make_double2(b + (double)fminf(a0, a1), b + (double)fmaxf(a0, a1));
+}
+
+// Per source column: [min, max] over rows of the unreduced x storage
+// coordinate.  Blocks of 32 columns (a lane each) by 8 warps over the rows.
+__global__ void __launch_bounds__(256) col_range_kernel(const float* q, const AxisEntry* ax,
+                                                        const double* bux, int n1x, int n1y,
+                                                        double2* out)
+{
+    const int lane = threadIdx.x % 32, w = threadIdx.x / 32;
+    const int nx = blockIdx.x * 32 + lane;
+    float lo = 3e38f, hi = -3e38f;
+    if (nx < n1x) {
+        for (int ny = w; ny < n1y; ny += 8) {
+            const float v = q[(size_t)ny * n1x + nx];
+            lo = fminf(lo, v);
+            hi = fmaxf(hi, v);
+        }
     }
-    out[nx] = make_double2(lo, hi);
+    __shared__ float red[2][8][32];
+    red[0][w][lane] = lo;
+    red[1][w][lane] = hi;
+    __syncthreads();
+    if (w == 0 && nx < n1x) {
+        for (int k = 1; k < 8; ++k) {
+            lo = fminf(lo, red[0][k][lane]);
+            hi = fmaxf(hi, red[1][k][lane]);
+        }
+        out[nx] = coord_range(bux[nx], ax[nx].s, lo, hi);
+    }
 }
 
 // Per source row: [min, max] over columns of the unreduced y storage coordinate.
@@ -172,19 +198,17 @@ __global__ void row_range_kernel(const float* q, const AxisEntry* ay, const doub
                                  double2* out)
 {
     const int ny = blockIdx.x;
-    const double b = buy[ny];
-    const float s = ay[ny].s;
-    double lo = 1e300, hi = -1e300;
+    float lo = 3e38f, hi = -3e38f;
     for (int nx = threadIdx.x; nx < n1x; nx += blockDim.x) {
-        const double g = b + (double)(s * q[(size_t)ny * n1x + nx]);
-        lo = fmin(lo, g);
-        hi = fmax(hi, g);
+        const float v = q[(size_t)ny * n1x + nx];
+        lo = fminf(lo, v);
+        hi = fmaxf(hi, v);
     }
     for (int o = 16; o > 0; o >>= 1) {
-        lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
-        hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+        lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
     }
-    __shared__ double red[2][32];
+    __shared__ float red[2][32];
     if ((threadIdx.x & 31) == 0) {
         red[0][threadIdx.x / 32] = lo;
         red[1][threadIdx.x / 32] = hi;
@@ -192,34 +216,38 @@ __global__ void row_range_kernel(const float* q, const AxisEntry* ay, const doub
     __syncthreads();
     if (threadIdx.x == 0) {
         for (int w = 1; w < (int)(blockDim.x / 32); ++w) {
-            lo = fmin(lo, red[0][w]);
-            hi = fmax(hi, red[1][w]);
+            lo = fminf(lo, red[0][w]);
+            hi = fmaxf(hi, red[1][w]);
         }
-        out[ny] = make_double2(lo, hi);
+        out[ny] = coord_range(buy[ny], ay[ny].s, lo, hi);
     }
 }
 
 // Minimum spacing on the fine grid of neighbouring samples: along x within a
-// row and along y within a column (one pair of minima per block).
+// row and along y within a column (one pair of minima per block).  A thread
+// takes one column over a chunk of rows: the FP64 difference of the
+// neighbouring columns' base coordinates is formed once, the q terms in
+// FP32 (the spacing is ~1 cell, so this is good to ~1e-6 cells).
 __global__ void min_step_kernel(const float* q, const AxisEntry* ax, const AxisEntry* ay,
                                 const double* bux, const double* buy, int n1x, int n1y,
                                 float2* out)
 {
-    const size_t total = (size_t)n1x * n1y;
+    const int nx = blockIdx.x * blockDim.x + threadIdx.x;
+    const int chunk = (n1y + gridDim.y - 1) / gridDim.y;
+    const int r0 = blockIdx.y * chunk, r1 = min(n1y, r0 + chunk);
     float mx = 3.0e38f, my = 3.0e38f;
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
-         i += (size_t)gridDim.x * blockDim.x) {
-        const int nx = (int)(i % n1x), ny = (int)(i / n1x);
-        const float qq = q[i];
-        if (nx + 1 < n1x) {
-            const double g0 = bux[nx] + (double)(ax[nx].s * qq);
-            const double g1 = bux[nx + 1] + (double)(ax[nx + 1].s * q[i + 1]);
-            mx = fminf(mx, (float)(g1 - g0));
-        }
-        if (ny + 1 < n1y) {
-            const double g0 = buy[ny] + (double)(ay[ny].s * qq);
-            const double g1 = buy[ny + 1] + (double)(ay[ny + 1].s * q[i + n1x]);
-            my = fminf(my, (float)(g1 - g0));
+    if (nx < n1x) {
+        const bool hasx = nx + 1 < n1x;
+        const float sx0 = ax[nx].s, sx1 = hasx ? ax[nx + 1].s : 0.f;
+        const float dbx = hasx ? (float)(bux[nx + 1] - bux[nx]) : 0.f;
+        for (int ny = r0; ny < r1; ++ny) {
+            const size_t i = (size_t)ny * n1x + nx;
+            const float qq = q[i];
+            if (hasx) mx = fminf(mx, dbx + (sx1 * q[i + 1] - sx0 * qq));
+            if (ny + 1 < n1y) {
+                const float dby = (float)(buy[ny + 1] - buy[ny]);
+                my = fminf(my, dby + (ay[ny + 1].s * q[i + n1x] - ay[ny].s * qq));
+            }
         }
     }
     for (int o = 16; o > 0; o >>= 1) {
@@ -237,7 +265,7 @@ __global__ void min_step_kernel(const float* q, const AxisEntry* ax, const AxisE
             mx = fminf(mx, red[0][w]);
             my = fminf(my, red[1][w]);
         }
-        out[blockIdx.x] = make_float2(mx, my);
+        out[blockIdx.y * gridDim.x + blockIdx.x] = make_float2(mx, my);
     }
 }
 
@@ -590,8 +618,8 @@ asfd_status plan_build_d1(asfd_plan_s* P, const double* d1, cudaStream_t st)
     P->band_clean = false;
     // 1. validate d1 without touching the plan's tables
     ASFD_CUDA(cudaMemsetAsync(P->status, 0, 2 * sizeof(unsigned), st));
-    d1_check_kernel<<<(unsigned)((nsrc + 255) / 256), 256, 0, st>>>(d1, nsrc, p.z0, P->status,
-                                                                   P->status + 1);
+    d1_check_kernel<<<(unsigned)((nsrc + 255) / 256), 256, 0, st>>>(
+        d1, nsrc, p.z0, (float)(1.0 / p.z0), P->status, P->status + 1);
     ASFD_CUDA(cudaGetLastError());
     unsigned hs[2] = {0, 0};
     ASFD_CUDA(cudaMemcpyAsync(hs, P->status, sizeof(hs), cudaMemcpyDeviceToHost, st));
@@ -614,7 +642,8 @@ asfd_status plan_build_d1(asfd_plan_s* P, const double* d1, cudaStream_t st)
                               cudaMemcpyDeviceToHost, st));
     ASFD_CUDA(cudaStreamSynchronize(st));
 
-    // 3. host binning: output tile -> list of source tiles (CSR over the band)
+    // 3. the band (fine-grid tiles that footprints reach) and the wrap flags,
+    //    from each source tile's footprint bounds
     const double hw = 0.5 * P->w + 1.0;  // half width plus a one-cell safety margin
     struct Range { int x0, x1, y0, y1; };
     std::vector<Range> rg(nst);
@@ -642,51 +671,56 @@ asfd_status plan_build_d1(asfd_plan_s* P, const double* d1, cudaStream_t st)
     }
     if (wrapx) { bx0 = 0; bx1 = P->ntx - 1; }
     if (wrapy) { by0 = 0; by1 = P->nty - 1; }
-    const int bntx = bx1 - bx0 + 1, bnty = by1 - by0 + 1;
-    const int ntiles = bntx * bnty;
-    std::vector<int> off(ntiles + 1, 0);
-    auto tmod = [](int v, int n) { int m = v % n; return m < 0 ? m + n : m; };
-    for (int t = 0; t < nst; ++t) {
-        const Range& r = rg[t];
-        for (int ty = r.y0; ty <= r.y1; ++ty)
-            for (int tx = r.x0; tx <= r.x1; ++tx) {
-                const int i = (tmod(ty, P->nty) - by0) * bntx + (tmod(tx, P->ntx) - bx0);
-                ++off[i + 1];
-            }
-    }
-    for (int i = 0; i < ntiles; ++i) off[i + 1] += off[i];
-    std::vector<int> lst(off[ntiles]);
-    std::vector<int> fillp(off.begin(), off.end() - 1);
-    for (int t = 0; t < nst; ++t) {
-        const Range& r = rg[t];
-        for (int ty = r.y0; ty <= r.y1; ++ty)
-            for (int tx = r.x0; tx <= r.x1; ++tx) {
-                const int i = (tmod(ty, P->nty) - by0) * bntx + (tmod(tx, P->ntx) - bx0);
-                lst[fillp[i]++] = t;
-            }
-    }
-    if (lst.size() > P->tile_src_cap || !P->tile_src) {
-        if (P->tile_src) release(P, P->tile_src);
-        P->tile_src = nullptr;
-        const size_t cap = std::max<size_t>(lst.size() + lst.size() / 4, 1024);
-        asfd_status s = alloc_n(P, &P->tile_src, cap);
-        if (s != ASFD_OK) { P->tile_src_cap = 0; return s; }
-        P->tile_src_cap = cap;
-    }
-    ASFD_CUDA(cudaMemcpyAsync(P->tile_off, off.data(), sizeof(int) * (ntiles + 1),
-                              cudaMemcpyHostToDevice, st));
-    if (!lst.empty())
-        ASFD_CUDA(cudaMemcpyAsync(P->tile_src, lst.data(), sizeof(int) * lst.size(),
-                                  cudaMemcpyHostToDevice, st));
-    ASFD_CUDA(cudaStreamSynchronize(st));
     P->band_tx0 = bx0;
     P->band_tx1 = bx1 + 1;
     P->band_ty0 = by0;
     P->band_ty1 = by1 + 1;
-    P->tile_pairs = (long long)lst.size();
     P->max_abs_eps = me;
     asfd_status cs = plan_build_colored(P, wrapx || wrapy, st);
     if (cs != ASFD_OK) return cs;
+    P->tile_pairs = 0;
+    if (!P->colored && !P->dense) {
+        // the shared-memory-atomic spread walks, per band tile, the source
+        // tiles whose footprints reach it: a CSR list built here
+        const int bntx = bx1 - bx0 + 1, bnty = by1 - by0 + 1;
+        const int ntiles = bntx * bnty;
+        std::vector<int> off(ntiles + 1, 0);
+        auto tmod = [](int v, int n) { int m = v % n; return m < 0 ? m + n : m; };
+        for (int t = 0; t < nst; ++t) {
+            const Range& r = rg[t];
+            for (int ty = r.y0; ty <= r.y1; ++ty)
+                for (int tx = r.x0; tx <= r.x1; ++tx) {
+                    const int i = (tmod(ty, P->nty) - by0) * bntx + (tmod(tx, P->ntx) - bx0);
+                    ++off[i + 1];
+                }
+        }
+        for (int i = 0; i < ntiles; ++i) off[i + 1] += off[i];
+        std::vector<int> lst(off[ntiles]);
+        std::vector<int> fillp(off.begin(), off.end() - 1);
+        for (int t = 0; t < nst; ++t) {
+            const Range& r = rg[t];
+            for (int ty = r.y0; ty <= r.y1; ++ty)
+                for (int tx = r.x0; tx <= r.x1; ++tx) {
+                    const int i = (tmod(ty, P->nty) - by0) * bntx + (tmod(tx, P->ntx) - bx0);
+                    lst[fillp[i]++] = t;
+                }
+        }
+        if (lst.size() > P->tile_src_cap || !P->tile_src) {
+            if (P->tile_src) release(P, P->tile_src);
+            P->tile_src = nullptr;
+            const size_t cap = std::max<size_t>(lst.size() + lst.size() / 4, 1024);
+            asfd_status s = alloc_n(P, &P->tile_src, cap);
+            if (s != ASFD_OK) { P->tile_src_cap = 0; return s; }
+            P->tile_src_cap = cap;
+        }
+        ASFD_CUDA(cudaMemcpyAsync(P->tile_off, off.data(), sizeof(int) * (ntiles + 1),
+                                  cudaMemcpyHostToDevice, st));
+        if (!lst.empty())
+            ASFD_CUDA(cudaMemcpyAsync(P->tile_src, lst.data(), sizeof(int) * lst.size(),
+                                      cudaMemcpyHostToDevice, st));
+        ASFD_CUDA(cudaStreamSynchronize(st));
+        P->tile_pairs = (long long)lst.size();
+    }
     if (P->learned && P->lfeat) {
         cs = learned_features(P, st);
         if (cs != ASFD_OK) return cs;
@@ -709,15 +743,21 @@ asfd_status plan_build_colored(asfd_plan_s* P, bool wraps, cudaStream_t st)
     P->windowed = false;
     P->dense = false;
     P->itemtile = false;
-    min_step_kernel<<<kStepBlocks, 256, 0, st>>>(P->q, P->ax, P->ay, P->bux, P->buy, p.n1x, p.n1y,
-                                                 P->step_min);
+    // a column per thread (blocks of 256 columns), rows in chunks, at most
+    // kStepBlocks blocks
+    static_assert((65536 + 255) / 256 <= kStepBlocks, "n1x <= 65536 fits one row of blocks");
+    const int sgx = (p.n1x + 255) / 256;
+    const int sgy = std::max(1, std::min(kStepBlocks / sgx, p.n1y));
+    min_step_kernel<<<dim3(sgx, sgy), 256, 0, st>>>(P->q, P->ax, P->ay, P->bux, P->buy, p.n1x,
+                                                    p.n1y, P->step_min);
     ASFD_CUDA(cudaGetLastError());
-    std::vector<float> sm(2 * kStepBlocks);
+    const int nsb = sgx * sgy;
+    std::vector<float> sm(2 * (size_t)nsb);
     ASFD_CUDA(cudaMemcpyAsync(sm.data(), P->step_min, sizeof(float) * sm.size(),
                               cudaMemcpyDeviceToHost, st));
     ASFD_CUDA(cudaStreamSynchronize(st));
     double msx = 3e38, msy = 3e38;
-    for (int b = 0; b < kStepBlocks; ++b) {
+    for (int b = 0; b < nsb; ++b) {
         msx = std::min(msx, (double)sm[2 * b]);
         msy = std::min(msy, (double)sm[2 * b + 1]);
     }
@@ -747,8 +787,8 @@ asfd_status plan_build_colored(asfd_plan_s* P, bool wraps, cudaStream_t st)
     if (!monotone || P->w > kMaxRingWidth) return ASFD_OK;
 
     // atomic-free tiles: row and column extents of the samples' coordinates
-    col_range_kernel<<<(p.n1x + 127) / 128, 128, 0, st>>>(P->q, P->ax, P->bux, p.n1x, p.n1y,
-                                                           P->col_range);
+    col_range_kernel<<<(p.n1x + 31) / 32, 256, 0, st>>>(P->q, P->ax, P->bux, p.n1x, p.n1y,
+                                                         P->col_range);
     row_range_kernel<<<p.n1y, 256, 0, st>>>(P->q, P->ay, P->buy, p.n1x, P->row_range);
     ASFD_CUDA(cudaGetLastError());
     std::vector<double> cr(2 * (size_t)p.n1x), rr(2 * (size_t)p.n1y);

@@ -52,22 +52,46 @@ struct ItemArgs {
 
 // First tap row and column of every sample (the spread's arithmetic), folded
 // into per-column-block and per-run ranges (min of the first tap, max of the
-// first tap + W).
+// first tap + W).  One warp per (column block, run), a lane per column: each
+// lane folds its column's rows, the warp folds its lanes, and one lane
+// merges the result with four atomics (all samples of a column block meet
+// in one entry, so per-sample atomics would serialise).
 __global__ void item_box_kernel(SpreadArgs a, int rows, int* xbox, int* ybox)
 {
-    const size_t total = (size_t)a.n1x * a.n1y;
-    for (size_t n = (size_t)blockIdx.x * blockDim.x + threadIdx.x; n < total;
-         n += (size_t)gridDim.x * blockDim.x) {
-        const int nx = (int)(n % a.n1x), ny = (int)(n / a.n1x);
-        int l0x, l0y;
-        float dx, dy;
-        sample_pos(a.ax[nx], a.ay[ny], a.px[nx], a.py[ny], __ldg(&a.q[n]), a.half_w, l0x, l0y, dx,
-                   dy);
-        const int w = (int)(2.f * a.half_w + 0.5f);
-        atomicMin(&xbox[2 * (nx / 32)], l0x);
-        atomicMax(&xbox[2 * (nx / 32) + 1], l0x + w);
-        atomicMin(&ybox[2 * (ny / rows)], l0y);
-        atomicMax(&ybox[2 * (ny / rows) + 1], l0y + w);
+    const int ncb = (a.n1x + 31) / 32, nruns = (a.n1y + rows - 1) / rows;
+    const int lane = threadIdx.x % 32;
+    const int w = (int)(2.f * a.half_w + 0.5f);
+    const int warps = gridDim.x * (blockDim.x / 32);
+    for (int item = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32; item < ncb * nruns;
+         item += warps) {
+        const int cb = item % ncb, run = item / ncb;
+        const int nx = cb * 32 + lane;
+        int xmin = INT_MAX, xmax = INT_MIN, ymin = INT_MAX, ymax = INT_MIN;
+        if (nx < a.n1x) {
+            const AxisEntry ex = a.ax[nx];
+            const AxisPos px = a.px[nx];
+            const int ny1 = min((run + 1) * rows, a.n1y);
+            for (int ny = run * rows; ny < ny1; ++ny) {
+                int l0x, l0y;
+                float dx, dy;
+                sample_pos(ex, a.ay[ny], px, a.py[ny], __ldg(&a.q[(size_t)ny * a.n1x + nx]),
+                           a.half_w, l0x, l0y, dx, dy);
+                xmin = min(xmin, l0x);
+                xmax = max(xmax, l0x);
+                ymin = min(ymin, l0y);
+                ymax = max(ymax, l0y);
+            }
+        }
+        xmin = __reduce_min_sync(0xffffffffu, xmin);
+        xmax = __reduce_max_sync(0xffffffffu, xmax);
+        ymin = __reduce_min_sync(0xffffffffu, ymin);
+        ymax = __reduce_max_sync(0xffffffffu, ymax);
+        if (lane == 0 && xmin <= xmax) {
+            atomicMin(&xbox[2 * cb], xmin);
+            atomicMax(&xbox[2 * cb + 1], xmax + w);
+            atomicMin(&ybox[2 * run], ymin);
+            atomicMax(&ybox[2 * run + 1], ymax + w);
+        }
     }
 }
 
@@ -194,33 +218,52 @@ __global__ void __launch_bounds__(32 * kItemWarps) spread_item_kernel(ItemArgs i
 
 // Band cell (x, y) = sum over the runs and then the column blocks whose item
 // boxes cover it of the items' tiles (fixed order).  xmap / ymap: first
-// column block (run) and count per band column (row).
-__global__ void item_gather_kernel(const float2* __restrict__ scratch, const int* __restrict__ xbox,
-                                   const int* __restrict__ ybox, const int* __restrict__ xmap,
-                                   const int* __restrict__ ymap, int x0, int y0, int bw, int bh,
-                                   int ncb, int tw, int th, float2* __restrict__ grid, int nfx)
+// column block (run) and count per band column (row).  A thread forms
+// kGatherRows cells of one band column: the column's boxes are looked up
+// once, and the rows' tile reads are independent of each other.
+constexpr int kGatherRows = 4;
+
+__global__ void __launch_bounds__(128)
+item_gather_kernel(const float2* __restrict__ scratch, const int* __restrict__ xbox,
+                   const int* __restrict__ ybox, const int* __restrict__ xmap,
+                   const int* __restrict__ ymap, int x0, int y0, int bw, int bh, int ncb, int tw,
+                   int th, float2* __restrict__ grid, int nfx)
 {
     const int bx = blockIdx.x * blockDim.x + threadIdx.x;
-    const int by = blockIdx.y;
-    if (bx >= bw || by >= bh) return;
-    const int x = x0 + bx, y = y0 + by;
-    const int xm = xmap[bx], ym = ymap[by];
+    if (bx >= bw) return;
+    const int x = x0 + bx;
+    const int xm = __ldg(&xmap[bx]);
     const int cb0 = xm & 0xffffff, ncx = xm >> 24;
-    const int rr0 = ym & 0xffffff, ncy = ym >> 24;
-    float2 s = make_float2(0.f, 0.f);
-    for (int j = 0; j < ncy; ++j) {
-        const int rr = rr0 + j;
-        const int ty = y - __ldg(&ybox[2 * rr]);
-        for (int k = 0; k < ncx; ++k) {
-            const int cb = cb0 + k;
-            const int tx = x - __ldg(&xbox[2 * cb]);
-            const float2 v =
-                __ldg(&scratch[((size_t)(rr * ncb + cb) * th + ty) * tw + tx]);
-            s.x += v.x;
-            s.y += v.y;
+    int tx[kItemMaxOverlap];
+#pragma unroll
+    for (int k = 0; k < kItemMaxOverlap; ++k) tx[k] = k < ncx ? x - __ldg(&xbox[2 * (cb0 + k)]) : 0;
+    const size_t tile = (size_t)th * tw;
+#pragma unroll
+    for (int r = 0; r < kGatherRows; ++r) {
+        const int by = blockIdx.y * kGatherRows + r;
+        if (by >= bh) break;
+        const int y = y0 + by;
+        const int ym = __ldg(&ymap[by]);
+        const int rr0 = ym & 0xffffff, ncy = ym >> 24;
+        float2 s = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int j = 0; j < kItemMaxOverlap; ++j) {
+            if (j < ncy) {
+                const int rr = rr0 + j;
+                const int ty = y - __ldg(&ybox[2 * rr]);
+                const float2* t = scratch + ((size_t)(rr * ncb + cb0) * th + ty) * tw;
+#pragma unroll
+                for (int k = 0; k < kItemMaxOverlap; ++k) {
+                    if (k < ncx) {
+                        const float2 v = __ldg(t + k * tile + tx[k]);
+                        s.x += v.x;
+                        s.y += v.y;
+                    }
+                }
+            }
         }
+        grid[(size_t)y * nfx + x] = s;
     }
-    grid[(size_t)y * nfx + x] = s;
 }
 
 asfd_status item_slots(int w, long long* slots)
@@ -285,7 +328,8 @@ asfd_status plan_build_itemtile(asfd_plan_s* P, cudaStream_t st)
                                                                                (int)(2 * ncb));
         item_box_init_kernel<<<(unsigned)((2 * nruns + 255) / 256), 256, 0, st>>>(P->it_ybox,
                                                                                  (int)(2 * nruns));
-        item_box_kernel<<<1024, 256, 0, st>>>(a, rows, P->it_xbox, P->it_ybox);
+        item_box_kernel<<<(unsigned)std::min<long long>((ncb * nruns + 7) / 8, 4096), 256, 0,
+                          st>>>(a, rows, P->it_xbox, P->it_ybox);
         ASFD_CUDA(cudaGetLastError());
         yb.assign(2 * nruns, 0);
         ASFD_CUDA(cudaMemcpyAsync(xb.data(), P->it_xbox, sizeof(int) * xb.size(),
@@ -372,7 +416,7 @@ asfd_status launch_spread_itemtile(asfd_plan_s* P, const float2* u1, cudaStream_
     if (e != cudaSuccess) return cuda_fail(e, "spread_item_kernel launch");
     const int bx0 = P->band_tx0 * kTileX, by0 = P->band_ty0 * kTileY;
     const int bw = (P->band_tx1 - P->band_tx0) * kTileX, bh = (P->band_ty1 - P->band_ty0) * kTileY;
-    item_gather_kernel<<<dim3((bw + 127) / 128, bh), 128, 0, st>>>(
+    item_gather_kernel<<<dim3((bw + 127) / 128, (bh + kGatherRows - 1) / kGatherRows), 128, 0, st>>>(
         P->rows, P->it_xbox, P->it_ybox, P->it_xmap, P->it_ymap, bx0, by0, bw, bh, P->it_ncb,
         P->it_tw, P->it_th, P->grid, P->nfx);
     e = cudaGetLastError();
