@@ -30,7 +30,7 @@ fft_rows_kernel(RowArgs a)
 }
 
 template <int L>
-__global__ void __launch_bounds__(ColCfg<L>::THREADS)
+__global__ void __launch_bounds__(ColCfg<L>::THREADS, ColCfgSel<L>::MIN_BLOCKS)
 fft_cols_kernel(ColArgs a)
 {
     extern __shared__ float2 sm[];
@@ -40,7 +40,7 @@ fft_cols_kernel(ColArgs a)
 // Adjoint column pass: h = conj(Cx Cy) gu2 placed at the kept bins, FFT with
 // e^{+i} along y, band rows [row0, row0 + nrows) stored to rows[s - row0][kx].
 template <int L>
-__global__ void __launch_bounds__(ColCfg<L>::THREADS)
+__global__ void __launch_bounds__(ColCfg<L>::THREADS, ColCfgSel<L>::MIN_BLOCKS)
 fft_cols_adj_kernel(const float2* __restrict__ g, int m2x, int m2y, const float2* __restrict__ cx,
                     const float2* __restrict__ cy, float2* __restrict__ rows, int row0, int nrows,
                     const float2* __restrict__ tw)
