@@ -57,19 +57,25 @@ __global__ void axis_table_kernel(AxisEntry* ae, AxisPos* ap, double* bu, int n,
 // m' = k' - m/2, times the global factor exp(ik z0) p1x p1y / (i lambda z0)
 // when `global` is set.  psi_hat(xi) = 2 sum_i w_i psi(z_i) cos(xi z_i)
 // (Gauss-Legendre on [0, w/2], nodes and weighted kernel values in quad).
+// A warp per entry: the lanes share the quadrature nodes and their partial
+// sums meet in a fixed shuffle tree.
 __global__ void dest_table_kernel(float2* C, int m, double p2, double lam_z0, int nf,
                                   const double* quad, int nq, int global, double two_z0_over_lam,
                                   double amp)
 {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= m) return;
+    const int k = (int)(((size_t)blockIdx.x * blockDim.x + threadIdx.x) / 32);
+    const int lane = threadIdx.x % 32;
+    if (k >= m) return;  // warp-uniform
     const int mp = k - m / 2;
+    double ph = 0.0;
+    for (int i = lane; i < nq; i += 32)
+        ph += quad[nq + i] * cospi(2.0 * (double)mp * quad[i] / (double)nf);
+    for (int o = 16; o > 0; o >>= 1) ph += __shfl_xor_sync(0xffffffffu, ph, o);
+    if (lane != 0) return;
+    ph *= 2.0;
     const double x2 = (double)mp * p2;
     double s, c;
     sincospi(reduce_halfturns(x2 * x2 / lam_z0), &s, &c);
-    double ph = 0.0;
-    for (int i = 0; i < nq; ++i) ph += quad[nq + i] * cospi(2.0 * (double)mp * quad[i] / (double)nf);
-    ph *= 2.0;
     const double sgn = (mp & 1) ? -1.0 : 1.0;
     double re = sgn * c / ph, im = sgn * s / ph;
     if (global) {
@@ -86,18 +92,29 @@ __global__ void dest_table_kernel(float2* C, int m, double p2, double lam_z0, in
 
 // Checks d1 (finite, below z0) and reduces max |d1|/z0 (in FP32: a bound
 // checked against 0.1).
-__global__ void d1_check_kernel(const double* d1, size_t n, double z0, float inv_z0,
-                                unsigned* status, unsigned* maxeps_bits)
+// (grid-stride; the block's maximum goes out with one atomic: per-warp
+// atomics on the one word serialise)
+__global__ void __launch_bounds__(256) d1_check_kernel(const double* d1, size_t n, double z0,
+                                                       float inv_z0, unsigned* status,
+                                                       unsigned* maxeps_bits)
 {
-    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     float e = 0.f;
-    if (i < n) {
+    bool bad = false;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x) {
         const double h = d1[i];
-        if (!isfinite(h) || !(h < z0)) atomicOr(status, kStatusBadD1);
-        else e = (float)fabs(h) * inv_z0;
+        if (!isfinite(h) || !(h < z0)) bad = true;
+        else e = fmaxf(e, (float)fabs(h) * inv_z0);
     }
+    if (bad) atomicOr(status, kStatusBadD1);
     for (int o = 16; o > 0; o >>= 1) e = fmaxf(e, __shfl_xor_sync(0xffffffffu, e, o));
-    if ((threadIdx.x & 31) == 0) atomicMax(maxeps_bits, __float_as_uint(e));
+    __shared__ float red[8];
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x / 32] = e;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < 8; ++w) e = fmaxf(e, red[w]);
+        atomicMax(maxeps_bits, __float_as_uint(e));
+    }
 }
 
 // q = d1 / (z0 - d1), stored FP32: z0 - d1 formed in FP64 (no cancellation
@@ -595,9 +612,9 @@ asfd_status plan_build_tables(asfd_plan_s* P, cudaStream_t st)
     P->nq = nq;
     ASFD_CUDA(cudaMemcpyAsync(P->quad, h.data(), sizeof(double) * 2 * nq, cudaMemcpyHostToDevice, st));
     const double amp = p.p1x * p.p1y / lam_z0;
-    dest_table_kernel<<<(p.m2x + 255) / 256, 256, 0, st>>>(P->cx, p.m2x, p.p2x, lam_z0, P->nfx,
+    dest_table_kernel<<<(p.m2x + 7) / 8, 256, 0, st>>>(P->cx, p.m2x, p.p2x, lam_z0, P->nfx,
                                                             P->quad, nq, 0, 0.0, 0.0);
-    dest_table_kernel<<<(p.m2y + 255) / 256, 256, 0, st>>>(P->cy, p.m2y, p.p2y, lam_z0, P->nfy,
+    dest_table_kernel<<<(p.m2y + 7) / 8, 256, 0, st>>>(P->cy, p.m2y, p.p2y, lam_z0, P->nfy,
                                                             P->quad, nq, 1, 2.0 * p.z0 / p.lambda,
                                                             amp);
     ASFD_CUDA(cudaGetLastError());
@@ -618,7 +635,7 @@ asfd_status plan_build_d1(asfd_plan_s* P, const double* d1, cudaStream_t st)
     P->band_clean = false;
     // 1. validate d1 without touching the plan's tables
     ASFD_CUDA(cudaMemsetAsync(P->status, 0, 2 * sizeof(unsigned), st));
-    d1_check_kernel<<<(unsigned)((nsrc + 255) / 256), 256, 0, st>>>(
+    d1_check_kernel<<<(unsigned)std::min<size_t>((nsrc + 255) / 256, 1216), 256, 0, st>>>(
         d1, nsrc, p.z0, (float)(1.0 / p.z0), P->status, P->status + 1);
     ASFD_CUDA(cudaGetLastError());
     unsigned hs[2] = {0, 0};
