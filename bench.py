@@ -839,10 +839,18 @@ def extra_measurements(args, g, u1, d1, pts, ref_pts, flush, stream):
                     for gb, _, _ in items]
             ms = time_device_ms(lambda: b.execute(u1s, out=outs), steps, 3, flush, stream)
             info = b.info()
+            b.set_schedule("persistent")
+            pms = time_device_ms(lambda: b.execute(u1s, out=outs), steps, 3, flush, stream)
+            pinfo = b.info()
         res["batch"] = {"workload": "rgb_batch24 (24 surfaces, 256^2..2048^2, 450/532/633 nm)",
                         "samples_per_s": info["source_samples"] / (ms * 1e-3), "ms": ms,
-                        "source_samples": info["source_samples"], "persistent_blocks": info["blocks"],
-                        "cuda_graph": bool(info["graph"])}
+                        "schedule": f"streams ({info['streams']} streams of the batch, CUDA graph)",
+                        "source_samples": info["source_samples"],
+                        "cuda_graph": bool(info["graph"]),
+                        "persistent": {"ms": pms,
+                                       "samples_per_s": info["source_samples"] / (pms * 1e-3),
+                                       "blocks": pinfo["blocks"],
+                                       "cuda_graph": bool(pinfo["graph"])}}
 
     return res
 

@@ -315,27 +315,43 @@ asfd_status asfd_learned_gradient(asfd_plan plan, const float* u1_dev, const flo
 
 /*
  * Batched transform of many surfaces (each with its own sizes, pitches,
- * wavelength, distance and height map) in ONE persistent cooperative kernel
- * per call, replayed through a CUDA graph: all spreads, a grid barrier, all
- * row FFTs, a grid barrier, all column FFTs with deconvolution and chirp.
+ * wavelength, distance and height map; one plan each), in one of two
+ * schedules, both replayed from CUDA graphs:
+ *   ASFD_BATCH_STREAMS (default): every surface's three kernels (spread, row
+ *     FFT, column FFT with deconvolution and chirp) in order on one of up to
+ *     8 streams of the batch, forked from and joined to the caller's stream;
+ *     surfaces are dealt to the streams largest first, each to the least
+ *     loaded, so that small surfaces fill the SMs that large ones leave idle.
+ *     The first call launches directly; later calls replay a graph of the
+ *     same launches, captured again when the field pointers change.
+ *   ASFD_BATCH_PERSISTENT: ONE persistent cooperative kernel per call: all
+ *     spreads, a grid barrier, all row FFTs, a grid barrier, all column FFTs
+ *     (one common kernel width in 4..8, fine grids up to 4096).
  */
 typedef struct asfd_batch_s* asfd_batch;
+
+enum { ASFD_BATCH_STREAMS = 0, ASFD_BATCH_PERSISTENT = 1 };
 
 typedef struct {
     int surfaces;
     int blocks, threads_per_block;   /* persistent grid (all blocks co-resident)      */
-    int spread_items, row_items, col_items;
-    int graph;                       /* 1 when the launch runs from a CUDA graph      */
+    int spread_items, row_items, col_items;  /* persistent schedule's items         */
+    int graph;                       /* 1 when the last call ran from a CUDA graph    */
     long long source_samples;        /* total over the batch                          */
+    int schedule;                    /* ASFD_BATCH_STREAMS or ASFD_BATCH_PERSISTENT  */
+    int persistent_ok;               /* 1 when the persistent schedule is available   */
+    int streams;                     /* streams of the stream schedule                */
 } asfd_batch_info;
 
 /*
  * params[count], d1_devs[count] (host arrays; d1 device FP64 [n1y][n1x] each,
- * read during the call).  All surfaces use the ES kernel with one common
- * width in 4..8 and fine grids up to 4096; otherwise ASFD_ERR_UNSUPPORTED.
- * Surfaces whose plan takes the atomic spreading kernel (folding, wrapping or
- * very densely packed samples) are spread by whole blocks, the others by
- * single warps, in the same launch.  Creates one plan per surface.  Errors as
+ * read during the call).  All surfaces use the ES kernel (else
+ * ASFD_ERR_UNSUPPORTED); the persistent schedule is available when they share
+ * one width in 4..8 and their fine grids are at most 4096 (in its launch,
+ * surfaces whose plan takes the atomic spreading kernel -- folding, wrapping
+ * or very densely packed samples -- are spread by whole blocks, the others by
+ * single warps).  Creates one plan per surface, with its work buffers, and
+ * the batch's streams; the schedule starts as ASFD_BATCH_STREAMS.  Errors as
  * asfd_plan_create.
  */
 asfd_status asfd_batch_create(asfd_batch* out, const asfd_params* params,
@@ -344,12 +360,21 @@ asfd_status asfd_batch_create(asfd_batch* out, const asfd_params* params,
 /*
  * Transform every surface: u1_devs[i] (device [n1y][n1x] complex of surface
  * i) -> u2_devs[i] (device [m2y][m2x] complex); host arrays of device
- * pointers.  Synchronises `stream` first (the previous launch must have read
- * the pointer table), then queues one graph launch.  Errors: ASFD_ERR_ARG,
- * ASFD_ERR_CUDA.
+ * pointers.  Stream schedule: queued on `stream` (its work forks to the
+ * batch's streams and joins back), asynchronous.  Persistent schedule:
+ * synchronises `stream` first (the previous launch must have read the
+ * pointer table), then queues one graph launch.  One batch serves one
+ * stream at a time.  Errors: ASFD_ERR_ARG, ASFD_ERR_CUDA.
  */
 asfd_status asfd_batch_execute(asfd_batch batch, const float* const* u1_devs,
                                float* const* u2_devs, void* stream);
+
+/*
+ * Choose the schedule of later asfd_batch_execute calls (ASFD_BATCH_STREAMS
+ * or ASFD_BATCH_PERSISTENT).  Errors: ASFD_ERR_ARG (NULL batch, unknown
+ * schedule), ASFD_ERR_UNSUPPORTED (persistent schedule not available).
+ */
+asfd_status asfd_batch_set_schedule(asfd_batch batch, int schedule);
 
 asfd_status asfd_batch_get_info(asfd_batch batch, asfd_batch_info* info);
 

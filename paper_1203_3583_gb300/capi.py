@@ -92,6 +92,7 @@ class BatchInfo(ctypes.Structure):
         ("surfaces", ctypes.c_int), ("blocks", ctypes.c_int), ("threads_per_block", ctypes.c_int),
         ("spread_items", ctypes.c_int), ("row_items", ctypes.c_int), ("col_items", ctypes.c_int),
         ("graph", ctypes.c_int), ("source_samples", ctypes.c_longlong),
+        ("schedule", ctypes.c_int), ("persistent_ok", ctypes.c_int), ("streams", ctypes.c_int),
     ]
 
 
@@ -100,6 +101,7 @@ SIGNATURES = {
                                  ctypes.POINTER(_vp), _int, _vp]),
     "asfd_batch_execute": (_int, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), _vp]),
     "asfd_batch_get_info": (_int, [_vp, ctypes.POINTER(BatchInfo)]),
+    "asfd_batch_set_schedule": (_int, [_vp, _int]),
     "asfd_batch_destroy": (_int, [_vp]),
     "asfd_plan_create": (_int, [ctypes.POINTER(_vp), ctypes.POINTER(Params), _vp, _vp]),
     "asfd_plan_update_d1": (_int, [_vp, _vp, _vp]),
@@ -185,6 +187,13 @@ def asfd_batch_execute(batch, u1_list, u2_list, stream=None) -> None:
     p1 = (_vp * n)(*[t.data_ptr() for t in u1_list])
     p2 = (_vp * n)(*[t.data_ptr() for t in u2_list])
     _check(load().asfd_batch_execute(batch, p1, p2, _stream(stream)))
+
+
+BATCH_SCHEDULES = {"streams": 0, "persistent": 1}
+
+
+def asfd_batch_set_schedule(batch, schedule: str) -> None:
+    _check(load().asfd_batch_set_schedule(batch, BATCH_SCHEDULES[schedule]))
 
 
 def asfd_batch_get_info(batch) -> dict:

@@ -126,7 +126,9 @@ class FresnelPlan:
 
 
 class FresnelBatch:
-    """Many surfaces in one persistent kernel per call (see asfd_batch_create)."""
+    """Many surfaces per call (see asfd_batch_create): schedule "streams"
+    (the default: each surface's kernels on one of the batch's streams) or
+    "persistent" (one cooperative kernel over the whole batch)."""
 
     def __init__(self, items, kernel_width: int = 7, sigma: float = 2.0, stream=None,
                  deterministic: bool = False):
@@ -144,6 +146,9 @@ class FresnelBatch:
             out = [torch.empty(s, dtype=torch.complex64, device="cuda") for s in self.shapes2]
         capi.asfd_batch_execute(self._handle, u1_list, out, stream)
         return out
+
+    def set_schedule(self, schedule: str) -> None:
+        capi.asfd_batch_set_schedule(self._handle, schedule)
 
     def info(self) -> dict:
         return capi.asfd_batch_get_info(self._handle)

@@ -205,9 +205,15 @@ def test_batch_multi_and_fft_checks_without_gpu(lib_path):
 
     p7 = capi.make_params(g)
     assert batch([p7], count=0) == 1
-    assert batch([p7, capi.make_params(g, kernel_width=5)]) == 5        # mixed widths
     assert batch([capi.make_params(g, kind=capi.ASFD_KERNEL_LEARNED, kernel_width=4)]) == 5
-    assert batch([capi.make_params(g, kernel_width=3)]) == 5            # batch widths 4..8
+    arr = (capi.Params * 2)(p7, p7)
+    d1s = (ctypes.c_void_p * 2)(fake, None)
+    out = ctypes.c_void_p()
+    assert lib.asfd_batch_create(ctypes.byref(out), arr, d1s, 2, None) == 1  # NULL d1
+    assert out.value is None
+    # (mixed widths, widths outside 4..8 and fine grids above 4096 are valid
+    # batches: only the persistent schedule is then unavailable)
+    assert lib.asfd_batch_set_schedule(None, 0) == 1
     # multi-surface sums: empty or NULL inputs
     plans = (ctypes.c_void_p * 1)(None)
     u1s = (ctypes.c_void_p * 1)(fake)
