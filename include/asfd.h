@@ -50,7 +50,8 @@ typedef enum {
     ASFD_ERR_ARG = 1,          /* invalid argument: sizes, NULL pointers, NaN d1, d1 >= z0 */
     ASFD_ERR_CUDA = 2,         /* a CUDA runtime call or kernel launch failed            */
     ASFD_ERR_NOMEM = 3,        /* device or host allocation failed                        */
-    ASFD_ERR_TIMEOUT = 4,      /* a bounded device-side wait ran out                      */
+    ASFD_ERR_TIMEOUT = 4,      /* a bounded device-side wait ran out (reserved: no kernel */
+                               /* of this library spins on a device flag, so none sets it) */
     ASFD_ERR_UNSUPPORTED = 5,  /* valid request outside what the library implements       */
     ASFD_ERR_STATE = 6         /* call not valid in the plan's current state              */
 } asfd_status;
