@@ -174,6 +174,15 @@ __global__ void __launch_bounds__(128) interp_window_kernel(InterpArgs a, int ro
 #pragma unroll
             for (int b = 0; b < W; ++b) load_row(b, R0 + b);
             live = true;
+        } else if (d == 2) {  // slide down two rows in one move (alpha > 1 takes
+                              // 1- and 2-row slides; two 1-row moves copy 12 rows)
+#pragma unroll
+            for (int b = 0; b + 2 < W; ++b)
+#pragma unroll
+                for (int i = 0; i < W; ++i) v[b][i] = v[b + 2][i];
+            load_row(W - 2, R0 + W);
+            load_row(W - 1, R0 + W + 1);
+            R0 = l0y;
         } else {
             for (int k = 0; k < d; ++k) {  // slide down one row
 #pragma unroll
