@@ -238,6 +238,11 @@ asfd_status plan_alloc_buffer(asfd_plan_s* P, void** p, size_t bytes);
 // a table).  Byte offsets of each inside a workspace, 256-byte aligned:
 // fine grid, row buffer, the host-execute staging of u1 and u2, and for
 // learned plans the training output and residual.
+// Kept columns per group of the row-FFT buffer's layout (fft_items.cuh), and
+// the buffer's row width: m2x rounded up to whole groups.
+constexpr int kRowGroup = 4;
+inline size_t row_buffer_width(int m2x) { return ((size_t)m2x + kRowGroup - 1) / kRowGroup * kRowGroup; }
+
 struct WorkLayout {
     size_t grid = 0, rows = 0, stage_u1 = 0, stage_u2 = 0, lu2 = 0, lres = 0, total = 0;
 };

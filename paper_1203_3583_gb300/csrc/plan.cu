@@ -489,7 +489,7 @@ WorkLayout work_layout(const asfd_params& p, int nfx, int nfy)
     L.grid = o;
     o += up(c * (size_t)nfx * nfy);
     L.rows = o;
-    o += up(c * (size_t)nfy * p.m2x);
+    o += up(c * (size_t)nfy * row_buffer_width(p.m2x));
     L.stage_u1 = o;
     o += up(c * (size_t)p.n1x * p.n1y);
     L.stage_u2 = o;
@@ -512,7 +512,7 @@ asfd_status plan_ensure_work(asfd_plan_s* P, unsigned need)
     if ((need & kWorkTransform) && !P->grid) {
         P->band_clean = false;  // fresh memory
         if ((s = alloc_n(P, &P->grid, (size_t)P->nfx * P->nfy)) != ASFD_OK) return s;
-        if ((s = alloc_n(P, &P->rows, (size_t)P->nfy * p.m2x)) != ASFD_OK) {
+        if ((s = alloc_n(P, &P->rows, (size_t)P->nfy * row_buffer_width(p.m2x))) != ASFD_OK) {
             release(P, P->grid);
             P->grid = nullptr;
             return s;

@@ -230,7 +230,7 @@ def test_batch_multi_and_fft_checks_without_gpu(lib_path):
 def test_workspace_bytes_without_gpu(lib_path):
     """asfd_workspace_bytes touches no device: its value is the sum of the
     work buffers' sizes (fine grid sigma m2x x sigma m2y, row buffer
-    sigma m2y x m2x, staging n1x n1y + m2x m2y, plus 2 m2x m2y for learned
+    sigma m2y x m2x rounded up to a multiple of 4, staging n1x n1y + m2x m2y, plus 2 m2x m2y for learned
     plans; complex64, each rounded up to 256 bytes), and 0 for invalid
     parameters."""
     from paper_1203_3583_gb300 import capi
@@ -248,6 +248,10 @@ def test_workspace_bytes_without_gpu(lib_path):
     g2 = dict(g, n1x=34, n1y=18, m2x=32, m2y=32)
     assert lib.asfd_workspace_bytes(capi.make_params(g2)) == (
         up(8 * 64 * 64) + up(8 * 64 * 32) + up(8 * 34 * 18) + up(8 * 32 * 32))
+    # the row buffer's width is m2x rounded up to the row pass's column groups of 4
+    g3 = dict(g, n1x=34, n1y=18, m2x=50, m2y=50)
+    assert lib.asfd_workspace_bytes(capi.make_params(g3, sigma=1.28)) == (
+        up(8 * 64 * 64) + up(8 * 64 * 52) + up(8 * 34 * 18) + up(8 * 50 * 50))
     assert lib.asfd_workspace_bytes(capi.make_params(dict(g, n1x=63))) == 0
     assert b"even" in lib.asfd_last_error()
     assert lib.asfd_workspace_bytes(None) == 0
