@@ -320,7 +320,7 @@ asfd_status asfd_learned_gradient(asfd_plan plan, const float* u1_dev, const flo
  * schedules, both replayed from CUDA graphs:
  *   ASFD_BATCH_STREAMS (default): every surface's three kernels (spread, row
  *     FFT, column FFT with deconvolution and chirp) in order on one of up to
- *     8 streams of the batch, forked from and joined to the caller's stream;
+ *     16 streams of the batch, forked from and joined to the caller's stream;
  *     surfaces are dealt to the streams largest first, each to the least
  *     loaded, so that small surfaces fill the SMs that large ones leave idle.
  *     The first call launches directly; later calls replay a graph of the

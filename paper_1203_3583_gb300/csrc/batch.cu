@@ -49,7 +49,7 @@ namespace {
 constexpr int kBatchThreads = 256;
 constexpr int kBatchWarps = kBatchThreads / 32;
 constexpr int kBatchMaxNf = 4096;  // persistent schedule: largest fine grid
-constexpr int kBatchStreams = 8;   // stream schedule: streams of a batch
+constexpr int kBatchStreams = 16;  // stream schedule: streams of a batch
 using BTile = ColoredTile<kTileX, kColTileY>;
 
 struct BatchSurf {

@@ -65,7 +65,7 @@ def test_batch_info(rgb_batch):
     assert info["source_samples"] == sum(g["n1x"] * g["n1y"] for g, _, _ in items)
     assert info["persistent_ok"] == 1 and info["blocks"] >= 1
     assert info["graph"] == 1
-    assert info["streams"] == 8
+    assert info["streams"] == 16
 
 
 def test_batch_equals_individual_plans(rgb_batch):
