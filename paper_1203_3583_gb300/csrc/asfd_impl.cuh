@@ -102,7 +102,7 @@ struct asfd_plan_s {
     // binning
     int ntx = 0, nty = 0;           // fine-grid tiles per axis
     int nstx = 0, nsty = 0;         // source tiles per axis
-    double4* src_bbox = nullptr;    // per source tile: unreduced footprint bounds (x0, x1, y0, y1)
+    float4* src_bbox = nullptr;     // per source tile: unreduced footprint bounds (x0, x1, y0, y1)
     int* tile_off = nullptr;        // [band tiles + 1] CSR offsets
     int* tile_src = nullptr;        // CSR source-tile ids
     int band_tx0 = 0, band_tx1 = 0, band_ty0 = 0, band_ty1 = 0;  // band in tiles

@@ -449,7 +449,6 @@ asfd_status asfd_batch_create(asfd_batch* out, const asfd_params* params,
     // the persistent kernel is instantiated for one common width in 4..8 and
     // fine grids up to kBatchMaxNf
     B->persistent_ok = common && w >= 4 && w <= 8;
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
     asfd_status s = [&]() -> asfd_status {
         ASFD_CUDA(cudaGetDevice(&B->device));
         for (int i = 0; i < count; ++i) {
@@ -515,7 +514,6 @@ asfd_status asfd_batch_create(asfd_batch* out, const asfd_params* params,
         batch_free(B);
         return fail(s, msg);
     }
-    (void)st;
     *out = B;
     return ASFD_OK;
 }

@@ -35,12 +35,17 @@ struct DirectGeom {
     double ox, oy;      // source grid offset
 };
 
+// The four FP64 terms of one source sample, 32-byte aligned (one load).
+struct alignas(32) DirectTerms {
+    double x, y, z, w;
+};
+
 // per sample: Eq. 5/7 {|x1|^2/(lambda r0) + 2 (s.x1 + (sz - 1) d1)/lambda,
 // 2 x1x/(lambda r0), 2 x1y/(lambda r0), 1/(lambda r0)} (the first term carries
 // u_I exp(-ik d1), 1 at normal incidence); Eq. 2 {x1x, x1y, z0 - d1,
 // 2 (s.x1 + sz d1)/lambda} (the phase of u_I)
 __global__ void direct_prep_kernel(DirectGeom g, const double* __restrict__ d1, int form,
-                                   double4* __restrict__ out)
+                                   DirectTerms* __restrict__ out)
 {
     const size_t n = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= (size_t)g.n1x * g.n1y) return;
@@ -49,11 +54,11 @@ __global__ void direct_prep_kernel(DirectGeom g, const double* __restrict__ d1, 
     const double h = d1[n];
     const double lin = g.sx * x + g.sy * y;
     if (form == 2) {
-        out[n] = make_double4(x, y, g.z0 - h, 2.0 * (lin + g.sz * h) / g.lambda);
+        out[n] = DirectTerms{x, y, g.z0 - h, 2.0 * (lin + g.sz * h) / g.lambda};
     } else {
         const double inv = 1.0 / (g.lambda * (g.z0 - h));
         const double inc = 2.0 * (lin + (g.sz - 1.0) * h) / g.lambda;
-        out[n] = make_double4((x * x + y * y) * inv + inc, 2.0 * x * inv, 2.0 * y * inv, inv);
+        out[n] = DirectTerms{(x * x + y * y) * inv + inc, 2.0 * x * inv, 2.0 * y * inv, inv};
     }
 }
 
@@ -64,7 +69,7 @@ __device__ __forceinline__ float reduce_halfturns(double h)
 
 template <int FORM>
 __global__ void __launch_bounds__(kDirectThreads)
-direct_sum_kernel(DirectGeom g, const double4* __restrict__ s, const float2* __restrict__ u1,
+direct_sum_kernel(DirectGeom g, const DirectTerms* __restrict__ s, const float2* __restrict__ u1,
                   int npts, const int* __restrict__ mx, const int* __restrict__ my,
                   float2* __restrict__ out)
 {
@@ -83,7 +88,7 @@ direct_sum_kernel(DirectGeom g, const double4* __restrict__ s, const float2* __r
     for (int j = 0; j < kDirectPoints; ++j) accr[j] = acci[j] = 0.0;
     const size_t total = (size_t)g.n1x * g.n1y;
     for (size_t n = threadIdx.x; n < total; n += kDirectThreads) {
-        const double4 t = s[n];
+        const DirectTerms t = s[n];
         const float2 u = __ldg(&u1[n]);
 #pragma unroll
         for (int j = 0; j < kDirectPoints; ++j) {
@@ -174,8 +179,8 @@ asfd_status direct_sum(const asfd_params* p, const double* d1, const float2* u1,
                  p->lambda, p->z0, p->incidence_sx, p->incidence_sy, sz, p->offset_x,
                  p->offset_y};
     const size_t n = (size_t)p->n1x * p->n1y;
-    double4* s = nullptr;
-    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&s), sizeof(double4) * n, st);
+    DirectTerms* s = nullptr;
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&s), sizeof(DirectTerms) * n, st);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return fail(ASFD_ERR_NOMEM, std::string("per-sample terms: ") + cudaGetErrorString(e));

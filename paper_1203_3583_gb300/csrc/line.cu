@@ -263,9 +263,10 @@ asfd_status asfd_line_destroy(asfd_line_plan P)
     if (!P) return ASFD_OK;
     int dev = -1;
     cudaGetDevice(&dev);
-    if (dev != P->device) cudaSetDevice(P->device);
+    const int own = P->device;  // P is gone after line_free
+    if (dev != own) cudaSetDevice(own);
     line_free(P);
-    if (dev != P->device && dev >= 0) cudaSetDevice(dev);
+    if (dev != own && dev >= 0) cudaSetDevice(dev);
     return ASFD_OK;
 }
 

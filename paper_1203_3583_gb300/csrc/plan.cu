@@ -132,7 +132,7 @@ __global__ void d1_q_kernel(const double* d1, float* q, size_t n, double z0)
 // in FP32 (within a few 1e-3 cells: the binning adds a one-cell margin).
 __global__ void src_bbox_kernel(const float* q, const AxisEntry* ax, const AxisEntry* ay,
                                 const double* bux, const double* buy, int n1x, int n1y, int nstx,
-                                double4* bbox)
+                                float4* bbox)
 {
     const int tile = blockIdx.x;
     const int nx = (tile % nstx) * kSrcTile + threadIdx.x % kSrcTile;
@@ -167,7 +167,7 @@ __global__ void src_bbox_kernel(const float* q, const AxisEntry* ax, const AxisE
             y0 = fminf(y0, red[2][w]);
             y1 = fmaxf(y1, red[3][w]);
         }
-        bbox[tile] = make_double4(x0, x1, y0, y1);
+        bbox[tile] = make_float4(x0, x1, y0, y1);
     }
 }
 
@@ -654,8 +654,8 @@ asfd_status plan_build_d1(asfd_plan_s* P, const double* d1, cudaStream_t st)
     src_bbox_kernel<<<nst, kSrcTile * kSrcTile, 0, st>>>(P->q, P->ax, P->ay, P->bux, P->buy, p.n1x,
                                                          p.n1y, P->nstx, P->src_bbox);
     ASFD_CUDA(cudaGetLastError());
-    std::vector<double> bb(4 * (size_t)nst);
-    ASFD_CUDA(cudaMemcpyAsync(bb.data(), P->src_bbox, sizeof(double) * 4 * nst,
+    std::vector<float> bb(4 * (size_t)nst);
+    ASFD_CUDA(cudaMemcpyAsync(bb.data(), P->src_bbox, sizeof(float) * 4 * nst,
                               cudaMemcpyDeviceToHost, st));
     ASFD_CUDA(cudaStreamSynchronize(st));
 
@@ -667,7 +667,7 @@ asfd_status plan_build_d1(asfd_plan_s* P, const double* d1, cudaStream_t st)
     bool wrapx = false, wrapy = false;
     int bx0 = P->ntx, bx1 = -1, by0 = P->nty, by1 = -1;
     for (int t = 0; t < nst; ++t) {
-        const double* b = &bb[4 * (size_t)t];
+        const float* b = &bb[4 * (size_t)t];
         Range r;
         r.x0 = (int)std::floor((b[0] - hw) / kTileX);
         r.x1 = (int)std::floor((b[1] + hw) / kTileX);
