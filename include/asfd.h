@@ -266,7 +266,7 @@ asfd_status asfd_adjoint(asfd_plan plan, const float* u1_dev, const float* grad_
  * and asfd_adjoint use the current model.
  */
 
-/* Number of floats of the learned model. */
+/* Number of floats of the learned model (a constant; no errors). */
 size_t asfd_learned_param_count(void);
 
 /* Copy the model to host memory (count must equal asfd_learned_param_count()).
@@ -295,7 +295,9 @@ asfd_status asfd_learned_train_step(asfd_plan plan, const float* u1_dev, const f
 /* Gradient of the same loss with respect to every model parameter (no
  * update), copied to grad_host (count = asfd_learned_param_count()); the loss
  * goes to loss_host if not NULL.  Synchronises `stream`.  For checking the
- * training kernels against an independent CPU computation. */
+ * training kernels against an independent CPU computation.  Errors:
+ * ASFD_ERR_ARG (NULL buffers, count not the model size), ASFD_ERR_STATE (not
+ * a learned plan), ASFD_ERR_NOMEM (work buffers), ASFD_ERR_CUDA. */
 asfd_status asfd_learned_gradient(asfd_plan plan, const float* u1_dev, const float* ref_u2_dev,
                                   float* grad_host, size_t count, double* loss_host, void* stream);
 
@@ -387,11 +389,13 @@ asfd_status asfd_get_plan_info(asfd_plan plan, asfd_plan_info* info);
 
 /* Wait for `stream`, then report a device-side failure recorded by the
  * plan's kernels since the last call (bounded waits, index checks), and
- * clear it.  ASFD_OK when none was recorded. */
+ * clear it.  ASFD_OK when none was recorded; else ASFD_ERR_STATE (an index
+ * check), ASFD_ERR_TIMEOUT (reserved); ASFD_ERR_ARG (NULL plan),
+ * ASFD_ERR_CUDA. */
 asfd_status asfd_check_device_status(asfd_plan plan, void* stream);
 
 /* Release the plan and everything it owns (synchronises the device).  NULL is
- * accepted. */
+ * accepted.  Always ASFD_OK. */
 asfd_status asfd_destroy(asfd_plan plan);
 
 /* Static description of a status code. */
@@ -465,7 +469,8 @@ asfd_status asfd_line_plan_create(asfd_line_plan* out, const asfd_line_params* p
                                   const double* x1_dev, const double* d1_dev, const double* w_dev,
                                   int n, void* stream);
 /* u1_dev: device complex[n] (in the plan's sample order); u2_dev: device
- * complex[m2].  Asynchronous on `stream`; calls on one plan must not overlap. */
+ * complex[m2].  Asynchronous on `stream`; calls on one plan must not overlap.
+ * Errors: ASFD_ERR_ARG (NULL), ASFD_ERR_UNSUPPORTED (width), ASFD_ERR_CUDA. */
 asfd_status asfd_line_execute(asfd_line_plan plan, const float* u1_dev, float* u2_dev,
                               void* stream);
 asfd_status asfd_line_destroy(asfd_line_plan plan);
@@ -498,7 +503,10 @@ asfd_status asfd_direct_sum(const asfd_params* p, const double* d1_dev, const fl
  * transform), exposed for unit tests and timing.  in_dev/out_dev: device
  * [lines][n] complex (may alias); n a power of two in [16, 16384];
  * sign = -1 computes X[k] = sum_j x[j] exp(-2 pi i jk/n), +1 the conjugate
- * kernel (no 1/n scaling).  Asynchronous.
+ * kernel (no 1/n scaling).  Asynchronous; the first call for a length on a
+ * device allocates and fills its twiddle table (and synchronises `stream`).
+ * Errors: ASFD_ERR_ARG (n, lines, sign, NULL buffers), ASFD_ERR_UNSUPPORTED
+ * (device ordinal above 63), ASFD_ERR_CUDA.
  */
 asfd_status asfd_fft_lines(int n, int lines, int sign, const float* in_dev, float* out_dev,
                            void* stream);
@@ -522,6 +530,7 @@ asfd_status asfd_fft_lines(int n, int lines, int sign, const float* in_dev, floa
  * and rewrites the n entries it reads before its transform, so calls that
  * can overlap on the GPU (different streams, or different host threads on
  * one device) race on the table and must be serialised by the caller.
+ * Errors: ASFD_ERR_ARG, ASFD_ERR_CUDA.
  */
 asfd_status asfd_fft_lines_noalloc(int n, int lines, int sign, const float* in_dev, float* out_dev,
                                    void* stream);
